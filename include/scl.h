@@ -1,0 +1,309 @@
+/*
+ * scl.h -- C ABI of the GB300 SparkCL per-partition offload library (libscl).
+ *
+ * SparkCL (Segal et al., 2015) runs a user kernel over the primitive arrays of
+ * one RDD partition on an accelerator: mapParameters() turns the partition
+ * into device buffers and sets the range (Sec. 3.1.1.1), run() executes once
+ * per element (Sec. 3.1.1.2), mapReturnValue() hands back a value or an array
+ * (Sec. 3.1.1.3); MapCL / MapCLPartition / ReduceCL apply that to an RDD and
+ * fold the partition results with a tree reduce (Sec. 3.1.3).  This library
+ * is that path on one GB300: load a partition (scl_load_partition*), run a
+ * map (scl_map), run a map fused with a reduce (scl_map_reduce,
+ * scl_keyed_reduce), return the value or array, and fold results across
+ * partitions (scl_combine*).  The user kernels are a fixed catalogue of
+ * hand-written sm_103a kernels (mix32, poly3, identity; sum / sum-min-max /
+ * keyed count+sum).  Around it: many partitions in one persistent launch
+ * (scl_batch_*), and a continuous-batching server (scl_server_*).
+ *
+ * Conventions
+ *   - Every call returns an int status: SCL_OK (0) or an SCL_E_* code.  No
+ *     call aborts, exits or throws across the ABI.  scl_last_error() gives a
+ *     message for the calling thread's most recent failure.
+ *   - Device memory: the caller hands scl_create an arena (any device buffer,
+ *     e.g. a torch uint8 tensor) that it owns and keeps alive until
+ *     scl_destroy.  The library sub-allocates partitions, outputs and its
+ *     scratch from that arena; it calls no cudaMalloc.  It does allocate a
+ *     few small pinned host staging buffers (cudaHostAlloc) at scl_create.
+ *   - Streams: a `void* stream` is a cudaStream_t owned by the caller (0 =
+ *     legacy default stream).  Calls named *_async only enqueue work; the
+ *     others synchronise that stream before returning.
+ *   - Host input pointers are read only during the call (the copy is
+ *     finished before an _async call returns unless the memory is pinned, in
+ *     which case it must stay untouched until the stream reaches the copy).
+ *   - Thread safety: calls on one context are serialised by a context lock.
+ *     Work enqueued by *_async calls of one context shares that context's
+ *     scratch: keep all *_async calls of a context on one stream.
+ */
+#ifndef SCL_H
+#define SCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCL_ABI_VERSION 1
+
+/* ------------------------------------------------------------ status codes */
+#define SCL_OK            0
+#define SCL_E_INVALID     1  /* bad handle, argument, dtype/kernel mismatch  */
+#define SCL_E_NOMEM       2  /* the arena has no free block large enough     */
+#define SCL_E_BUDGET      3  /* admission would exceed the HBM budget        */
+#define SCL_E_KEY_RANGE   4  /* a key outside [0, num_keys) was seen (pair skipped) */
+#define SCL_E_TIMEOUT     5  /* a bounded wait gave up                        */
+#define SCL_E_PENDING     6  /* server task not finished yet                  */
+#define SCL_E_CUDA        7  /* a CUDA runtime call failed (message has text) */
+#define SCL_E_STATE       8  /* call not valid in the current state           */
+#define SCL_E_UNSUPPORTED 9  /* combination not in the kernel catalogue      */
+
+/* --------------------------------------------------------------- the types */
+typedef struct scl_ctx scl_ctx;      /* one library context on one device     */
+typedef struct scl_batch scl_batch;  /* a planned batch of partition tasks    */
+typedef uint64_t scl_part;           /* opaque partition handle (0 = none)    */
+
+/* Element type of a partition's primitive arrays (Sec. 3.1.1.1: partitions
+ * are turned into arrays of primitive types before the kernel runs). */
+typedef enum {
+    SCL_U32 = 0,          /* uint32_t[n]                                  */
+    SCL_I32 = 1,          /* int32_t[n] (same 32-bit patterns as SCL_U32) */
+    SCL_F32 = 2,          /* float[n]                                     */
+    SCL_KV_I32_F32 = 3    /* int32_t keys[n] + float vals[n], two arrays  */
+} scl_dtype;
+
+/* The catalogue of map kernels (the run() body, Sec. 3.1.1.2). */
+typedef enum {
+    SCL_K_IDENT = 0,      /* y = x                                          */
+    SCL_K_MIX32 = 1,      /* 32-bit x: x^=x>>16; x*=0x7feb352d; x^=x>>15;
+                             x*=0x846ca68b; x^=x>>16 (mod 2^32)             */
+    SCL_K_POLY3 = 2       /* fp32 x: t = fma(c0, x*x, c1); y = fma(t, x, c2),
+                             x*x rounded once; default c = {0.5, -1.25, 0.1} */
+} scl_map_kernel;
+
+/* The catalogue of reductions (ReduceCL, Sec. 3.1.3 item 3; the reduce-by-key
+ * of the WordCount demo, Sec. 3.2.3). */
+typedef enum {
+    SCL_R_NONE = 0,             /* map only (scl_map)                        */
+    SCL_R_SUM = 1,              /* U32/I32: uint64 sum (mod 2^64) of y as
+                                   unsigned; F32: sum                         */
+    SCL_R_SUM_MIN_MAX = 2,      /* F32: sum, min, max of y                   */
+    SCL_R_KEYED_COUNT_SUM = 3   /* KV: per key count (uint32) and sum        */
+} scl_reduce;
+
+/* Context configuration. */
+typedef struct {
+    int32_t device;              /* CUDA device ordinal                        */
+    int32_t reserved0;
+    void* arena;                 /* device buffer the library sub-allocates;
+                                    caller-owned, 256-byte aligned             */
+    uint64_t arena_bytes;        /* its size                                   */
+    uint64_t hbm_budget_bytes;   /* server admission budget; 0 = arena_bytes   */
+    int32_t inflight_batches;    /* server: batches in flight at once (1..16)  */
+    int32_t reserved1;
+    const char* tune_cache_path; /* autotune cache file; NULL = none           */
+} scl_config;
+
+/* Result of one partition's map+reduce (the value mapReturnValue returns,
+ * Sec. 3.1.1.3).  48 bytes, same layout on host and device.
+ *   SUM on U32/I32:       u64_sum
+ *   SUM / SUM_MIN_MAX on F32: f64_sum (fp64 fold of the partial sums),
+ *                         f32_sum (f64_sum rounded), f32_min, f32_max
+ *                         (NaN ignored; empty: +inf / -inf)
+ *   KEYED_COUNT_SUM:      u64_sum = pairs counted, f64_sum = their value sum
+ *   n:                    elements (pairs) in the partition
+ *   status:               SCL_OK or SCL_E_KEY_RANGE                        */
+typedef struct {
+    uint64_t u64_sum;
+    double f64_sum;
+    float f32_sum;
+    float f32_min;
+    float f32_max;
+    int32_t status;
+    uint64_t n;
+    uint32_t kind;       /* internal kernel id that produced it */
+    uint32_t reserved;
+} scl_result;
+
+/* One partition task of a batch or of the server. 64 bytes.
+ * Keyed tasks write their tables to device arrays the caller owns:
+ * counts_out[num_keys] (uint32), sums_out[num_keys] (float) and, if not NULL,
+ * sums64_out[num_keys] (double, the fp64 fold before rounding).            */
+typedef struct {
+    scl_part part;
+    int32_t kernel;      /* scl_map_kernel                                  */
+    int32_t reduce;      /* scl_reduce                                      */
+    uint32_t num_keys;   /* keyed: 1..4096                                  */
+    float coef[3];       /* poly3 coefficients                              */
+    uint32_t* counts_out;
+    float* sums_out;
+    double* sums64_out;
+    uint64_t reserved;
+} scl_task;
+
+/* ------------------------------------------------------------- errors, info */
+
+/* Static text for a status code. Never NULL. */
+const char* scl_strerror(int status);
+
+/* Message of the calling thread's last failed call ("" if none).  The pointer
+ * stays valid until that thread's next call into the library. */
+const char* scl_last_error(void);
+
+/* ABI version (SCL_ABI_VERSION of the built library). */
+int scl_abi_version(void);
+
+/* Total kernel launches this library has made in the process (a graph
+ * replay counts each kernel node), for launch accounting. */
+int scl_kernel_launches_total(uint64_t* out);
+
+/* ---------------------------------------------------------------- contexts */
+
+/* Create a context on cfg->device over the caller's arena.  Queries the
+ * device (SM count, L2 size), carves the scratch region from the arena and
+ * loads autotuned launch shapes from cfg->tune_cache_path if it exists.
+ * Errors: SCL_E_INVALID (NULL args, misaligned or too small arena),
+ * SCL_E_CUDA. */
+int scl_create(const scl_config* cfg, scl_ctx** out);
+
+/* Destroy a context: stops the server if running, frees host staging.
+ * The arena is not touched (the caller frees it). NULL is a no-op. */
+int scl_destroy(scl_ctx* ctx);
+
+/* Bytes of the arena still free / the largest free block. */
+int scl_arena_stats(scl_ctx* ctx, uint64_t* free_bytes, uint64_t* largest_block);
+
+/* ------------------------------------------------------------- partitions */
+
+/* mapParameters, data side (Sec. 3.1.1.1): copy one host primitive array of
+ * n elements into a new arena-resident partition.  `host` may be pageable or
+ * pinned; the copy is enqueued on `stream` and, for pageable memory, finished
+ * before return.  n = 0 is allowed (an empty partition).
+ * Errors: SCL_E_INVALID (dtype is KV, NULL host with n>0), SCL_E_NOMEM. */
+int scl_load_partition(scl_ctx* ctx, const void* host, scl_dtype dtype,
+                       uint64_t n, void* stream, scl_part* out);
+
+/* Same for a keyed partition: keys[n] int32 and vals[n] float (SoA). */
+int scl_load_partition_kv(scl_ctx* ctx, const int32_t* keys, const float* vals,
+                          uint64_t n, void* stream, scl_part* out);
+
+/* Wrap caller-owned device arrays as a partition without copying (e.g. a
+ * torch tensor's data_ptr).  dev1 is the value array for SCL_KV_I32_F32 and
+ * must be NULL otherwise.  The arrays must outlive the handle.  Any
+ * alignment is accepted (16-byte aligned arrays take the vector path). */
+int scl_wrap_device(scl_ctx* ctx, void* dev0, void* dev1, scl_dtype dtype,
+                    uint64_t n, scl_part* out);
+
+/* Release a partition (returns its arena block if the library owns it). */
+int scl_free_partition(scl_ctx* ctx, scl_part part);
+
+/* Describe a partition: dtype, length and device pointers (dev1 NULL unless
+ * keyed).  Any output pointer may be NULL. */
+int scl_partition_info(scl_ctx* ctx, scl_part part, scl_dtype* dtype,
+                       uint64_t* n, void** dev0, void** dev1);
+
+/* Copy a partition's array(s) back to host memory (mapReturnValue returning
+ * an array, Sec. 3.1.1.3).  host0 receives n elements; host1 the values of a
+ * keyed partition (may be NULL otherwise).  Synchronous on `stream`. */
+int scl_read_partition(scl_ctx* ctx, scl_part part, void* host0, void* host1,
+                       void* stream);
+
+/* ------------------------------------------------------------ map / reduce */
+
+/* MapCL with an output array (Sec. 3.1.3 item 1; Fig. 3's c[gid] = f(a[gid])):
+ * allocate a partition of the same dtype and length and write y = map(x) to
+ * it.  Kernels: MIX32 on U32/I32, POLY3 on F32, IDENT on U32/I32/F32 (copy).
+ * `coef` is read for POLY3 (NULL = default).  Enqueued on `stream`; the
+ * handle is usable for stream-ordered work at once.
+ * Errors: SCL_E_UNSUPPORTED, SCL_E_NOMEM, SCL_E_INVALID. */
+int scl_map(scl_ctx* ctx, scl_part in, scl_map_kernel kernel,
+            const float coef[3], void* stream, scl_part* out);
+
+/* MapCLPartition + ReduceCL over one partition, fused into one pass
+ * (Sec. 3.1.3 items 2-3): y = map(x) for every element, folded by `reduce`.
+ * Valid (kernel, reduce, dtype): {IDENT, MIX32} x SUM on U32/I32;
+ * {IDENT, POLY3} x {SUM, SUM_MIN_MAX} on F32.  Writes *out (host) and
+ * synchronises `stream`.  Integer sums are exact; fp32 sums are fp32 within
+ * 64 KB segments folded in fp64 in a fixed order, so a result is bitwise
+ * reproducible and identical whether the partition runs alone or in a batch
+ * of the same context.  Empty partition: sums 0, min +inf, max -inf. */
+int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
+                   const float coef[3], scl_reduce reduce, void* stream,
+                   scl_result* out);
+
+/* The same, enqueue-only: the result is written to device memory `dev_out`
+ * (one scl_result) when the stream reaches it. */
+int scl_map_reduce_async(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
+                         const float coef[3], scl_reduce reduce, void* stream,
+                         scl_result* dev_out);
+
+/* Keyed reduce of one KV partition (the reduce-by-key of Sec. 3.2.3):
+ * counts_out[k] = number of pairs with key k (exact), sums_out[k] = their
+ * value sum (fp32 accumulation per block, fp64 across blocks, rounded), and
+ * sums64_out[k] the fp64 value (NULL to skip).  All outputs are HOST arrays
+ * of num_keys (1..4096) entries.  Pairs with a key outside [0, num_keys)
+ * are skipped and the call returns SCL_E_KEY_RANGE after writing the tables
+ * of the valid pairs.  `result` (may be NULL) receives the totals. */
+int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys,
+                     void* stream, uint32_t* counts_out, float* sums_out,
+                     double* sums64_out, scl_result* result);
+
+/* Enqueue-only keyed reduce; outputs are DEVICE arrays (sums64 may be NULL),
+ * dev_result (device, may be NULL) gets the totals and status. */
+int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,
+                           void* stream, uint32_t* counts_out, float* sums_out,
+                           double* sums64_out, scl_result* dev_result);
+
+/* ----------------------------------------------- ReduceCL across partitions */
+
+/* Host tree-combine of k per-partition results (ReduceCL's treeReduce,
+ * Sec. 3.1.3 item 3 and Sec. 3.2.2): sums add (uint64 mod 2^64; fp64 by a
+ * pairwise tree), min of mins, max of maxes, n adds; status is the first
+ * non-OK status.  k = 0 gives the empty result. Pure host code. */
+int scl_combine(const scl_result* parts, uint32_t k, scl_result* out);
+
+/* Host merge of k keyed tables, row-major [k][num_keys]: counts add, fp64
+ * sums add by a pairwise tree.  sums64 may be NULL (then only counts). */
+int scl_combine_keyed(const uint32_t* counts, const double* sums64, uint32_t k,
+                      uint32_t num_keys, uint32_t* counts_out,
+                      double* sums64_out);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Plan many partition tasks as ONE persistent launch (thousands of uneven
+ * partitions; the paper's "enough data" concern, Sec. 3 item 2, and kernel
+ * caching per worker, Sec. 3.1.1.2).  The plan, task table and scratch are
+ * placed in the arena; nothing runs yet.  Tasks keep referencing their
+ * partitions: those must stay alive while the batch exists. */
+int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
+                     scl_batch** out);
+
+/* Enqueue the batch on `stream` (its CUDA graph if one was captured, else a
+ * direct launch).  Results land in device memory; read them with
+ * scl_batch_results.  Launches of one batch must not overlap (use one
+ * stream or order them). */
+int scl_batch_launch(scl_batch* batch, void* stream);
+
+/* Capture the batch's launch into a CUDA graph on `stream` (which must not
+ * be capturing already); later scl_batch_launch calls replay it. */
+int scl_batch_capture(scl_batch* batch, void* stream);
+
+/* Copy the last launch's results to host results[ntasks] after synchronising
+ * `stream`.  Returns SCL_E_KEY_RANGE if any task saw a bad key. */
+int scl_batch_results(scl_batch* batch, void* stream, scl_result* results);
+
+/* Launches of your kernels one launch of this batch makes (for accounting). */
+int scl_batch_kernel_launches(scl_batch* batch, uint32_t* count);
+
+/* Free the batch (its graph and arena blocks). NULL is a no-op. */
+int scl_batch_destroy(scl_batch* batch);
+
+/* One-shot: create, launch, read results, destroy. */
+int scl_batch_run(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
+                  void* stream, scl_result* results);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCL_H */

@@ -1,0 +1,546 @@
+// capi.cu -- the extern "C" entry points declared in include/scl.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "runtime.h"
+#include "server.h"
+
+namespace scl {
+const char* last_error();
+uint64_t launches_total();
+}  // namespace scl
+
+using namespace scl;
+
+namespace {
+
+struct DeviceGuard {
+    explicit DeviceGuard(int dev) { cudaSetDevice(dev); }
+};
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define CTX_ENTER(ctx)                                                     \
+    if (!(ctx)) return fail(SCL_E_INVALID, "null context");               \
+    clear_error();                                                         \
+    std::lock_guard<std::recursive_mutex> lock_((ctx)->mu);               \
+    DeviceGuard dg_((ctx)->device)
+
+size_t dtype_words(scl_dtype dt) { return dt == SCL_KV_I32_F32 ? 2 : 1; }
+
+double pairwise_sum(const scl_result* r, uint32_t lo, uint32_t hi) {
+    if (hi - lo == 1) return r[lo].f64_sum;
+    const uint32_t mid = lo + (hi - lo) / 2;
+    return pairwise_sum(r, lo, mid) + pairwise_sum(r, mid, hi);
+}
+
+}  // namespace
+
+struct scl_batch {
+    Ctx* ctx = nullptr;
+    Plan plan;
+    PlanImage img;
+    KernelArgs args;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t ntasks = 0;
+    std::vector<scl_result> host_results;
+};
+
+extern "C" {
+
+const char* scl_strerror(int status) {
+    switch (status) {
+        case SCL_OK: return "ok";
+        case SCL_E_INVALID: return "invalid argument";
+        case SCL_E_NOMEM: return "arena out of memory";
+        case SCL_E_BUDGET: return "HBM admission budget exceeded";
+        case SCL_E_KEY_RANGE: return "key out of range";
+        case SCL_E_TIMEOUT: return "timed out";
+        case SCL_E_PENDING: return "pending";
+        case SCL_E_CUDA: return "CUDA error";
+        case SCL_E_STATE: return "invalid state";
+        case SCL_E_UNSUPPORTED: return "unsupported combination";
+        default: return "unknown status";
+    }
+}
+
+const char* scl_last_error(void) { return last_error(); }
+
+int scl_abi_version(void) { return SCL_ABI_VERSION; }
+
+int scl_kernel_launches_total(uint64_t* out) {
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    *out = launches_total();
+    return SCL_OK;
+}
+
+// ---------------------------------------------------------------- contexts
+
+int scl_create(const scl_config* cfg, scl_ctx** out) {
+    clear_error();
+    if (!cfg || !out) return fail(SCL_E_INVALID, "null argument");
+    *out = nullptr;
+    if (!cfg->arena || cfg->arena_bytes < (1u << 20))
+        return fail(SCL_E_INVALID, "arena must be a device buffer of at least 1 MiB");
+    if ((uintptr_t)cfg->arena % kAlign)
+        return fail(SCL_E_INVALID, "arena must be 256-byte aligned");
+    int ndev = 0;
+    SCL_CUDA(cudaGetDeviceCount(&ndev));
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(SCL_E_INVALID, "device %d not present (%d devices)", cfg->device, ndev);
+    SCL_CUDA(cudaSetDevice(cfg->device));
+    cudaPointerAttributes pa;
+    SCL_CUDA(cudaPointerGetAttributes(&pa, cfg->arena));
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+        return fail(SCL_E_INVALID, "arena is not device memory");
+
+    scl_ctx* c = new (std::nothrow) scl_ctx();
+    if (!c) return fail(SCL_E_NOMEM, "host allocation failed");
+    c->device = cfg->device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device);
+    c->arena.init((char*)cfg->arena, cfg->arena_bytes);
+    c->d_result = (scl_result*)c->arena.alloc(sizeof(scl_result));
+    c->d_kout = (uint32_t*)c->arena.alloc((size_t)kMaxKeys * 16);
+    int st = SCL_OK;
+    if (!c->d_result || !c->d_kout) st = fail(SCL_E_NOMEM, "arena too small");
+    if (st == SCL_OK && cudaHostAlloc((void**)&c->h_result, sizeof(scl_result),
+                                      cudaHostAllocDefault) != cudaSuccess)
+        st = fail(SCL_E_CUDA, "cudaHostAlloc failed");
+    if (st == SCL_OK) st = ensure_scratch(c, &c->single, 1, 0, 0, kMaxKeys / kFoldBlock);
+    if (st == SCL_OK && cfg->tune_cache_path) {
+        c->tune_path = cfg->tune_cache_path;
+        st = load_tuning(c, cfg->tune_cache_path);
+    }
+    if (st != SCL_OK) {
+        if (c->h_result) cudaFreeHost(c->h_result);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SCL_OK;
+}
+
+int scl_server_stop(scl_ctx* ctx);
+
+int scl_destroy(scl_ctx* ctx) {
+    if (!ctx) return SCL_OK;
+    scl_server_stop(ctx);
+    {
+        std::lock_guard<std::recursive_mutex> g(ctx->mu);
+        cudaSetDevice(ctx->device);
+        if (ctx->h_result) cudaFreeHost(ctx->h_result);
+    }
+    delete ctx;
+    return SCL_OK;
+}
+
+int scl_arena_stats(scl_ctx* ctx, uint64_t* free_bytes, uint64_t* largest_block) {
+    if (!ctx) return fail(SCL_E_INVALID, "null context");
+    if (free_bytes) *free_bytes = ctx->arena.free_bytes();
+    if (largest_block) *largest_block = ctx->arena.largest_free();
+    return SCL_OK;
+}
+
+// -------------------------------------------------------------- partitions
+
+static int new_partition(scl_ctx* c, scl_dtype dt, uint64_t n, Partition* p) {
+    const size_t bytes = align_up(n * 4);
+    void* b = c->arena.alloc(bytes * dtype_words(dt));
+    if (!b) return fail(SCL_E_NOMEM, "arena: no block for a partition of %llu elements",
+                        (unsigned long long)n);
+    p->dtype = dt;
+    p->n = n;
+    p->block = b;
+    p->d0 = b;
+    p->d1 = dt == SCL_KV_I32_F32 ? (char*)b + bytes : nullptr;
+    return SCL_OK;
+}
+
+static scl_part register_partition(scl_ctx* c, const Partition& p) {
+    const scl_part h = c->next_part++;
+    c->parts[h] = p;
+    return h;
+}
+
+int scl_load_partition(scl_ctx* ctx, const void* host, scl_dtype dtype, uint64_t n,
+                       void* stream, scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    if (dtype != SCL_U32 && dtype != SCL_I32 && dtype != SCL_F32)
+        return fail(SCL_E_INVALID, "scl_load_partition takes U32, I32 or F32 (use _kv for keyed)");
+    if (n && !host) return fail(SCL_E_INVALID, "null host pointer");
+    Partition p;
+    SCL_TRY(new_partition(ctx, dtype, n, &p));
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(p.d0, host, n * 4, cudaMemcpyHostToDevice, S(stream));
+        if (e != cudaSuccess) {
+            ctx->arena.release(p.block);
+            return fail(SCL_E_CUDA, "H2D copy failed: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = register_partition(ctx, p);
+    return SCL_OK;
+}
+
+int scl_load_partition_kv(scl_ctx* ctx, const int32_t* keys, const float* vals, uint64_t n,
+                          void* stream, scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    if (n && (!keys || !vals)) return fail(SCL_E_INVALID, "null host pointer");
+    Partition p;
+    SCL_TRY(new_partition(ctx, SCL_KV_I32_F32, n, &p));
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(p.d0, keys, n * 4, cudaMemcpyHostToDevice, S(stream));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p.d1, vals, n * 4, cudaMemcpyHostToDevice, S(stream));
+        if (e != cudaSuccess) {
+            ctx->arena.release(p.block);
+            return fail(SCL_E_CUDA, "H2D copy failed: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = register_partition(ctx, p);
+    return SCL_OK;
+}
+
+int scl_wrap_device(scl_ctx* ctx, void* dev0, void* dev1, scl_dtype dtype, uint64_t n,
+                    scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    if ((int)dtype < 0 || dtype > SCL_KV_I32_F32) return fail(SCL_E_INVALID, "bad dtype");
+    if (n && !dev0) return fail(SCL_E_INVALID, "null device pointer");
+    if (dtype == SCL_KV_I32_F32 && n && !dev1)
+        return fail(SCL_E_INVALID, "keyed partition needs a value array");
+    if (dtype != SCL_KV_I32_F32 && dev1)
+        return fail(SCL_E_INVALID, "dev1 must be NULL for non-keyed partitions");
+    if (((uintptr_t)dev0 | (uintptr_t)dev1) % 4)
+        return fail(SCL_E_INVALID, "arrays must be 4-byte aligned");
+    Partition p{dtype, n, dev0, dev1, nullptr};
+    *out = register_partition(ctx, p);
+    return SCL_OK;
+}
+
+int scl_free_partition(scl_ctx* ctx, scl_part part) {
+    CTX_ENTER(ctx);
+    auto it = ctx->parts.find(part);
+    if (it == ctx->parts.end()) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (it->second.block) {
+        // stream-ordered work may still read it
+        SCL_CUDA(cudaDeviceSynchronize());
+        ctx->arena.release(it->second.block);
+    }
+    ctx->parts.erase(it);
+    return SCL_OK;
+}
+
+int scl_partition_info(scl_ctx* ctx, scl_part part, scl_dtype* dtype, uint64_t* n, void** dev0,
+                       void** dev1) {
+    CTX_ENTER(ctx);
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (dtype) *dtype = p->dtype;
+    if (n) *n = p->n;
+    if (dev0) *dev0 = p->d0;
+    if (dev1) *dev1 = p->d1;
+    return SCL_OK;
+}
+
+int scl_read_partition(scl_ctx* ctx, scl_part part, void* host0, void* host1, void* stream) {
+    CTX_ENTER(ctx);
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (p->n && !host0) return fail(SCL_E_INVALID, "null host pointer");
+    if (p->n) {
+        SCL_CUDA(cudaMemcpyAsync(host0, p->d0, p->n * 4, cudaMemcpyDeviceToHost, S(stream)));
+        if (p->d1 && host1)
+            SCL_CUDA(cudaMemcpyAsync(host1, p->d1, p->n * 4, cudaMemcpyDeviceToHost, S(stream)));
+    }
+    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    return SCL_OK;
+}
+
+// ------------------------------------------------------------ map / reduce
+
+int scl_map(scl_ctx* ctx, scl_part in, scl_map_kernel kernel, const float coef[3], void* stream,
+            scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    const Partition* p = ctx->part(in);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    uint32_t kind;
+    if (p->dtype == SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "scl_map takes a 1-array partition");
+    if (kernel == SCL_K_IDENT) kind = K_U32_IDENT;
+    else if (kernel == SCL_K_MIX32 && p->dtype != SCL_F32) kind = K_U32_MIX32;
+    else if (kernel == SCL_K_POLY3 && p->dtype == SCL_F32) kind = K_F32_POLY3;
+    else return fail(SCL_E_UNSUPPORTED, "map kernel %d does not apply to dtype %d", (int)kernel,
+                     (int)p->dtype);
+    const Partition src = *p;
+    Partition o;
+    SCL_TRY(new_partition(ctx, src.dtype, src.n, &o));
+    if (src.n) {
+        static const float kDef[3] = {0.5f, -1.25f, 0.1f};
+        const float* cf = coef ? coef : kDef;
+        const int aligned = ((uintptr_t)src.d0 % 16) == 0;
+        const void* fn = map_kernel_fn((int)kind, aligned);
+        const int blk = map_kernel_block();
+        const uint64_t chunk = (uint64_t)blk * map_kernel_ipt() * 4;
+        uint64_t want = aligned ? (src.n + chunk - 1) / chunk : (src.n + blk - 1) / blk;
+        uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->sms * 8));
+        void* dst = o.d0;
+        const void* sp = src.d0;
+        uint64_t n = src.n;
+        float a = cf[0], b = cf[1], cc = cf[2];
+        void* params[] = {(void*)&sp, (void*)&dst, (void*)&n, &a, &b, &cc};
+        cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(blk), params, 0, S(stream));
+        if (e != cudaSuccess) {
+            ctx->arena.release(o.block);
+            return fail(SCL_E_CUDA, "map launch failed: %s", cudaGetErrorString(e));
+        }
+        count_launches(1);
+    }
+    *out = register_partition(ctx, o);
+    return SCL_OK;
+}
+
+static int map_reduce_common(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
+                             const float coef[3], scl_reduce reduce, void* stream,
+                             scl_result* dev_out) {
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    uint32_t kind;
+    if (reduce == SCL_R_KEYED_COUNT_SUM)
+        return fail(SCL_E_UNSUPPORTED, "use scl_keyed_reduce for keyed partitions");
+    SCL_TRY(resolve_kind(p->dtype, kernel, reduce, &kind));
+    return run_single(ctx, *p, kind, coef, 0, nullptr, nullptr, nullptr, dev_out, S(stream));
+}
+
+int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const float coef[3],
+                   scl_reduce reduce, void* stream, scl_result* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    SCL_TRY(map_reduce_common(ctx, part, kernel, coef, reduce, stream, ctx->d_result));
+    SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
+                             cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    *out = *ctx->h_result;
+    return SCL_OK;
+}
+
+int scl_map_reduce_async(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const float coef[3],
+                         scl_reduce reduce, void* stream, scl_result* dev_out) {
+    CTX_ENTER(ctx);
+    if (!dev_out) return fail(SCL_E_INVALID, "null device result pointer");
+    return map_reduce_common(ctx, part, kernel, coef, reduce, stream, dev_out);
+}
+
+static int keyed_common(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                        uint32_t* counts, float* sums, double* sums64, scl_result* dres) {
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (p->dtype != SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "partition is not keyed");
+    if (num_keys < 1 || num_keys > kMaxKeys)
+        return fail(SCL_E_INVALID, "num_keys %u not in [1, %u]", num_keys, kMaxKeys);
+    return run_single(ctx, *p, K_KEYED, nullptr, num_keys, counts, sums, sums64, dres, S(stream));
+}
+
+int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                     uint32_t* counts_out, float* sums_out, double* sums64_out,
+                     scl_result* result) {
+    CTX_ENTER(ctx);
+    if (!counts_out || !sums_out) return fail(SCL_E_INVALID, "null output table");
+    uint32_t* dc = ctx->d_kout;
+    float* ds = (float*)(ctx->d_kout + kMaxKeys);
+    double* d64 = (double*)(ctx->d_kout + 2 * kMaxKeys);
+    SCL_TRY(keyed_common(ctx, part, num_keys, stream, dc, ds, d64, ctx->d_result));
+    SCL_CUDA(cudaMemcpyAsync(counts_out, dc, num_keys * 4, cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaMemcpyAsync(sums_out, ds, num_keys * 4, cudaMemcpyDeviceToHost, S(stream)));
+    if (sums64_out)
+        SCL_CUDA(cudaMemcpyAsync(sums64_out, d64, num_keys * 8, cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
+                             cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    if (result) *result = *ctx->h_result;
+    if (ctx->h_result->status == SCL_E_KEY_RANGE)
+        return fail(SCL_E_KEY_RANGE, "a key outside [0, %u) was skipped", num_keys);
+    return SCL_OK;
+}
+
+int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                           uint32_t* counts_out, float* sums_out, double* sums64_out,
+                           scl_result* dev_result) {
+    CTX_ENTER(ctx);
+    if (!counts_out || !sums_out) return fail(SCL_E_INVALID, "null output table");
+    return keyed_common(ctx, part, num_keys, stream, counts_out, sums_out, sums64_out,
+                        dev_result ? dev_result : ctx->d_result);
+}
+
+// ----------------------------------------------------------------- combine
+
+int scl_combine(const scl_result* parts, uint32_t k, scl_result* out) {
+    clear_error();
+    if (!out || (k && !parts)) return fail(SCL_E_INVALID, "null argument");
+    scl_result r;
+    memset(&r, 0, sizeof r);
+    r.f32_min = INFINITY;
+    r.f32_max = -INFINITY;
+    r.status = SCL_OK;
+    for (uint32_t i = 0; i < k; ++i) {
+        r.u64_sum += parts[i].u64_sum;
+        r.n += parts[i].n;
+        if (parts[i].f32_min == parts[i].f32_min && parts[i].f32_min < r.f32_min)
+            r.f32_min = parts[i].f32_min;
+        if (parts[i].f32_max == parts[i].f32_max && parts[i].f32_max > r.f32_max)
+            r.f32_max = parts[i].f32_max;
+        if (r.status == SCL_OK && parts[i].status != SCL_OK) r.status = parts[i].status;
+    }
+    if (k) {
+        r.f64_sum = pairwise_sum(parts, 0, k);
+        r.kind = parts[0].kind;
+    }
+    r.f32_sum = (float)r.f64_sum;
+    *out = r;
+    return SCL_OK;
+}
+
+int scl_combine_keyed(const uint32_t* counts, const double* sums64, uint32_t k, uint32_t num_keys,
+                      uint32_t* counts_out, double* sums64_out) {
+    clear_error();
+    if (!counts_out || (k && !counts) || (sums64 && !sums64_out))
+        return fail(SCL_E_INVALID, "null argument");
+    std::vector<double> col(k);
+    for (uint32_t j = 0; j < num_keys; ++j) {
+        uint32_t c = 0;
+        for (uint32_t i = 0; i < k; ++i) c += counts[(size_t)i * num_keys + j];
+        counts_out[j] = c;
+        if (sums64) {
+            // pairwise tree over the k partitions
+            for (uint32_t i = 0; i < k; ++i) col[i] = sums64[(size_t)i * num_keys + j];
+            uint32_t m = k;
+            while (m > 1) {
+                uint32_t h = (m + 1) / 2;
+                for (uint32_t i = 0; i + h < m; ++i) col[i] += col[i + h];
+                m = h;
+            }
+            sums64_out[j] = k ? col[0] : 0.0;
+        }
+    }
+    return SCL_OK;
+}
+
+// ----------------------------------------------------------------- batches
+
+int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks, scl_batch** out) {
+    CTX_ENTER(ctx);
+    if (!out || (ntasks && !tasks)) return fail(SCL_E_INVALID, "null argument");
+    *out = nullptr;
+    scl_batch* b = new (std::nothrow) scl_batch();
+    if (!b) return fail(SCL_E_NOMEM, "host allocation failed");
+    b->ctx = ctx;
+    b->ntasks = ntasks;
+    int st = plan_tasks(ctx, tasks, ntasks, &b->plan);
+    std::vector<char> host;
+    if (st == SCL_OK && ntasks) st = build_image(ctx, b->plan, &b->img, &host, &b->args);
+    if (st == SCL_OK && ntasks) {
+        if (cudaMemcpy(b->img.block, host.data(), b->img.plan_bytes, cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes) != cudaSuccess)
+            st = fail(SCL_E_CUDA, "uploading the batch plan failed");
+    }
+    if (st != SCL_OK) {
+        if (b->img.block) ctx->arena.release(b->img.block);
+        delete b;
+        return st;
+    }
+    b->host_results.resize(ntasks);
+    *out = b;
+    return SCL_OK;
+}
+
+int scl_batch_launch(scl_batch* b, void* stream) {
+    if (!b) return fail(SCL_E_INVALID, "null batch");
+    CTX_ENTER(b->ctx);
+    if (b->exec) {
+        SCL_CUDA(cudaGraphLaunch(b->exec, S(stream)));
+        count_launches(1 + (b->plan.fold_tasks.empty() ? 0 : 1));
+        return SCL_OK;
+    }
+    return launch_plan(b->ctx, b->plan, b->args, S(stream));
+}
+
+int scl_batch_capture(scl_batch* b, void* stream) {
+    if (!b) return fail(SCL_E_INVALID, "null batch");
+    CTX_ENTER(b->ctx);
+    if (b->exec) return SCL_OK;
+    SCL_CUDA(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
+    const uint64_t before = launches_total();
+    int st = launch_plan(b->ctx, b->plan, b->args, S(stream));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(S(stream), &g);
+    count_launches(0 - (launches_total() - before));   // capture launched nothing
+    if (st != SCL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(SCL_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(SCL_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    b->graph = g;
+    b->exec = x;
+    return SCL_OK;
+}
+
+int scl_batch_results(scl_batch* b, void* stream, scl_result* results) {
+    if (!b) return fail(SCL_E_INVALID, "null batch");
+    CTX_ENTER(b->ctx);
+    if (b->ntasks && !results) return fail(SCL_E_INVALID, "null results");
+    if (b->ntasks)
+        SCL_CUDA(cudaMemcpyAsync(results, b->img.results, b->ntasks * sizeof(scl_result),
+                                 cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    for (uint32_t i = 0; i < b->ntasks; ++i)
+        if (results[i].status == SCL_E_KEY_RANGE)
+            return fail(SCL_E_KEY_RANGE, "task %u saw a key out of range", i);
+    return SCL_OK;
+}
+
+int scl_batch_kernel_launches(scl_batch* b, uint32_t* count) {
+    if (!b || !count) return fail(SCL_E_INVALID, "null argument");
+    *count = b->ntasks ? 1u + (b->plan.fold_tasks.empty() ? 0u : 1u) : 0u;
+    return SCL_OK;
+}
+
+int scl_batch_destroy(scl_batch* b) {
+    if (!b) return SCL_OK;
+    {
+        std::lock_guard<std::recursive_mutex> g(b->ctx->mu);
+        cudaSetDevice(b->ctx->device);
+        cudaDeviceSynchronize();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        if (b->img.block) b->ctx->arena.release(b->img.block);
+    }
+    delete b;
+    return SCL_OK;
+}
+
+int scl_batch_run(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks, void* stream,
+                  scl_result* results) {
+    scl_batch* b = nullptr;
+    SCL_TRY(scl_batch_create(ctx, tasks, ntasks, &b));
+    int st = scl_batch_launch(b, stream);
+    if (st == SCL_OK) st = scl_batch_results(b, stream, results);
+    std::string keep = last_error();
+    scl_batch_destroy(b);
+    if (st != SCL_OK) return fail(st, "%s", keep.c_str());
+    return SCL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// internal.h -- structures shared by the sm_103a kernels and the host runtime
+// of libscl.  Not part of the ABI (include/scl.h is).
+//
+// Execution model.  A launch runs a set of partition tasks.  Each task is one
+// partition with one catalogue kernel (SparkCL's per-partition kernel run,
+// Sec. 3.1.1-3.1.3).  Two kinds of work units exist:
+//   * streaming segments: a task of a streaming kind (uint32 sum, fp32
+//     sum/min/max) is cut into fixed segments whose length depends only on the
+//     partition length and the launch shape; CTAs of a persistent grid pull
+//     segments from one global counter; every segment leaves one partial in
+//     its own slot, and the CTA that finishes a task's last segment folds the
+//     slots in slot order (one atomic ticket per task).
+//   * keyed pieces: keyed tasks are split by the host planner into contiguous
+//     pieces, an even share of the keyed work per CTA; each CTA accumulates
+//     its piece into a shared-memory table and writes the table to its slot;
+//     a second, small kernel folds the slots of multi-piece tasks.
+#pragma once
+
+#include <stdint.h>
+
+#include "scl.h"
+
+namespace scl {
+
+constexpr uint32_t kMaxKeys = 4096;                 // shared-memory table entries
+constexpr uint32_t kKeyedTableWords = 2 * kMaxKeys; // count[kMaxKeys] then sum[kMaxKeys]
+constexpr uint32_t kKeyedSmemBytes = kKeyedTableWords * 4;
+constexpr uint64_t kKeyedPieceAlign = 64;           // piece boundaries, in pairs
+constexpr uint64_t kKeyedMinPiece = 32768;          // pairs; keeps table flushes cheap
+constexpr uint64_t kKeyedTaskOverhead = 4096;       // pair-equivalents per keyed task
+constexpr uint32_t kMaxSegChunks = 4;               // a streaming segment is 1..4 chunks
+constexpr uint32_t kTargetSegsPerTask = 256;
+constexpr uint32_t kFoldBlock = 256;                // keyed fold kernel block size
+
+// Work kinds: (map kernel, reduce) combinations of the catalogue.
+enum Kind : uint32_t {
+    K_U32_IDENT = 0,   // uint64 sum of raw uint32
+    K_U32_MIX32 = 1,   // uint64 sum of mix32(x)
+    K_F32_IDENT = 2,   // sum / min / max of raw fp32
+    K_F32_POLY3 = 3,   // sum / min / max of poly3(x)
+    K_KEYED = 4,       // per-key count / sum
+    K_NUM = 5
+};
+
+// Which kinds a compiled persistent kernel contains.
+enum Mask : uint32_t { M_U32 = 0, M_F32 = 1, M_KEYED = 2, M_ALL = 3, M_NUM = 4 };
+
+__host__ __device__ constexpr bool mask_has_u32(int m) { return m == M_U32 || m == M_ALL; }
+__host__ __device__ constexpr bool mask_has_f32(int m) { return m == M_F32 || m == M_ALL; }
+__host__ __device__ constexpr bool mask_has_keyed(int m) { return m == M_KEYED || m == M_ALL; }
+__host__ __device__ constexpr bool mask_has_stream(int m) { return m != M_KEYED; }
+
+enum TaskFlags : uint32_t { TF_ALIGNED = 1u };  // in0 (and in1) 16-byte aligned
+
+struct alignas(16) DevTask {
+    const void* in0;        // values, or keys for K_KEYED
+    const void* in1;        // values for K_KEYED
+    scl_result* result;     // device result slot
+    uint32_t* counts_out;   // keyed outputs (device)
+    float* sums_out;
+    double* sums64_out;     // may be null
+    uint64_t n;             // elements / pairs
+    uint32_t kind;
+    uint32_t num_keys;
+    uint32_t nseg;          // streaming segments or keyed pieces of this task
+    uint32_t slot0;         // first partial slot of this task
+    uint32_t seg_elems;     // streaming segment length (elements)
+    uint32_t flags;
+    float coef[3];
+    uint32_t seg_base;      // first global streaming segment of this task
+};
+static_assert(sizeof(DevTask) == 96, "DevTask layout");
+
+struct KPiece {             // one keyed piece: pairs [begin, end) of a task
+    uint64_t begin, end;
+    uint32_t task, slot;
+};
+static_assert(sizeof(KPiece) == 24, "KPiece layout");
+
+struct alignas(16) StreamPartial {  // one streaming segment's partial
+    double s;       // fp64 sum (fp32 kinds)
+    uint64_t u;     // uint64 sum (uint32 kinds)
+    float mn, mx;
+    uint32_t pad[2];
+};
+static_assert(sizeof(StreamPartial) == 32, "StreamPartial layout");
+
+// Header words of a launch's scratch.
+enum HdrWord : uint32_t { H_QUEUE = 0, H_EXIT = 1, H_ERROR = 2, H_FOLD_EXIT = 3, H_WORDS = 16 };
+
+struct KernelArgs {
+    const DevTask* tasks;       // null: single-task mode, the task is `single`
+    const uint32_t* seg_task;   // global streaming segment -> task (batch mode)
+    const uint32_t* kp_first;   // [grid + 1] first keyed piece of each CTA (batch mode)
+    const KPiece* kpieces;
+    const uint32_t* fold_tasks; // keyed tasks with more than one piece (batch mode)
+    StreamPartial* spart;       // streaming partial slots
+    uint32_t* kpart;            // keyed partial tables, kKeyedTableWords words per slot
+    StreamPartial* fpart;       // keyed fold: one partial per (fold task, key block)
+    uint32_t* tickets;          // per task; zero between launches
+    uint32_t* task_flags;       // per task; bit 0 = a key was out of range
+    uint32_t* hdr;              // H_WORDS words
+    uint32_t nseg_stream;       // total streaming segments
+    uint32_t nkeyed_ctas;       // single-task keyed mode: number of pieces
+    uint32_t nfold;             // entries of fold_tasks (batch mode)
+    uint32_t pad;
+    DevTask single;
+};
+
+// Geometry of a streaming task's segments, shared by host planning and tests.
+__host__ __device__ inline uint32_t stream_seg_elems(uint64_t n, uint32_t chunk) {
+    uint64_t per = (uint64_t)chunk * kTargetSegsPerTask;
+    uint64_t c = (n + per - 1) / per;
+    if (c < 1) c = 1;
+    if (c > kMaxSegChunks) c = kMaxSegChunks;
+    return (uint32_t)(c * chunk);
+}
+
+__host__ __device__ inline uint32_t stream_nseg(uint64_t n, uint32_t seg_elems) {
+    uint64_t s = (n + seg_elems - 1) / seg_elems;
+    return s < 1 ? 1u : (uint32_t)s;
+}
+
+// Single-task keyed pieces: piece c of G covers [B(c), B(c+1)).
+__host__ __device__ inline uint64_t keyed_single_bound(uint64_t n, uint32_t c, uint32_t G) {
+    if (c == 0) return 0;
+    if (c >= G) return n;
+    uint64_t b = (uint64_t)c * n / G;   // c < 2^20, n < 2^43 in practice: no overflow
+    return b / kKeyedPieceAlign * kKeyedPieceAlign;
+}
+
+__host__ __device__ inline uint32_t keyed_single_pieces(uint64_t n, uint32_t grid) {
+    uint64_t g = (n + kKeyedMinPiece - 1) / kKeyedMinPiece;
+    if (g < 1) g = 1;
+    if (g > grid) g = grid;
+    return (uint32_t)g;
+}
+
+// Host-side launch entry of one compiled persistent-kernel instantiation.
+struct KernelEntry {
+    int mask, block, ipt;
+    const void* fn;                    // __global__ function pointer
+    size_t dyn_smem;                   // dynamic shared memory per CTA
+};
+
+// Provided by the kernel translation units.
+extern const KernelEntry* kernel_table(int mask, int* count);
+extern const void* fold_kernel_fn();
+extern const void* map_kernel_fn(int kind, int aligned);
+extern int map_kernel_block();
+extern int map_kernel_ipt();
+
+}  // namespace scl

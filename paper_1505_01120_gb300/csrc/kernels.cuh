@@ -1,0 +1,589 @@
+// kernels.cuh -- sm_103a kernels of the SparkCL per-partition path.
+//
+//   k_persistent<BLOCK, IPT, MASK>  MapCLPartition + ReduceCL fused (Sec. 3.1.3
+//                                   items 2-3): every element of a partition is
+//                                   mapped by the catalogue kernel (the run()
+//                                   body of Sec. 3.1.1.2) and folded, in one
+//                                   HBM pass, by a persistent grid.
+//   k_keyed_fold                    second pass of the keyed reduce (Sec. 3.2.3):
+//                                   folds the per-piece tables of keyed tasks.
+//   k_map<BLOCK, IPT, KIND, ALIGNED> MapCL with a materialised output array
+//                                   (Sec. 3.1.3 item 1; Fig. 3's c[gid] = f(a[gid])).
+//
+// Data path: 128-bit vector loads (ld.global.nc, no L1 allocation, 256-byte L2
+// prefetch) of IPT independent vectors per thread before any use, so a CTA
+// has BLOCK*IPT*16 bytes in flight; streaming sums are fp32 per thread per
+// chunk, fp64 across chunks, a fixed-order warp-butterfly and block tree, one
+// partial per segment and one atomic ticket per task; the last CTA of a task
+// folds the segment partials in slot order (deterministic).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace scl {
+namespace dev {
+
+// ----------------------------------------------------------------- loads
+
+__device__ __forceinline__ uint4 ld_stream_v4(const void* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_b32(const void* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_stream_v4(void* p, uint4 v) {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};"
+                 :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+
+// ------------------------------------------------------- catalogue maps
+
+// mix32: xorshift-multiply finaliser on 32-bit words (all steps mod 2^32).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// poly3: t = fma(a, x*x, b); y = fma(t, x, c); the product x*x rounded once.
+// Explicit _rn intrinsics so that no contraction can change the roundings.
+__device__ __forceinline__ float poly3(float x, float a, float b, float c) {
+    const float x2 = __fmul_rn(x, x);
+    const float t = __fmaf_rn(a, x2, b);
+    return __fmaf_rn(t, x, c);
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t map_u32(uint32_t x) {
+    if constexpr (KIND == K_U32_MIX32) return mix32(x);
+    else return x;
+}
+
+template <int KIND>
+__device__ __forceinline__ float map_f32(float x, float a, float b, float c) {
+    if constexpr (KIND == K_F32_POLY3) return poly3(x, a, b, c);
+    else return x;
+}
+
+// ------------------------------------------------------ block reductions
+
+struct RedSmem {
+    double d[32];
+    unsigned long long u[32];
+    float mn[32];
+    float mx[32];
+    uint32_t q;      // next streaming segment (prefetched by thread 0)
+    uint32_t flag;   // broadcast: this CTA folds the task
+};
+
+// Every thread returns the block total.  Fixed association order:
+// a xor-butterfly within each warp, then the same butterfly over the warp
+// totals.  Ends with a barrier so the smem can be reused at once.
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, RedSmem& sm) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm.u[w] = v;
+    __syncthreads();
+    v = (l < BLOCK / 32) ? sm.u[l] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_reduce_f(double& s, float& mn, float& mx, RedSmem& sm) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sm.d[w] = s;
+        sm.mn[w] = mn;
+        sm.mx[w] = mx;
+    }
+    __syncthreads();
+    const bool in = l < BLOCK / 32;
+    s = in ? sm.d[l] : 0.0;
+    mn = in ? sm.mn[l] : CUDART_INF_F;
+    mx = in ? sm.mx[l] : -CUDART_INF_F;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void write_result(scl_result* r, uint64_t u, double s, float mn,
+                                             float mx, int32_t status, uint64_t n,
+                                             uint32_t kind) {
+    scl_result o;
+    o.u64_sum = u;
+    o.f64_sum = s;
+    o.f32_sum = (float)s;
+    o.f32_min = mn;
+    o.f32_max = mx;
+    o.status = status;
+    o.n = n;
+    o.kind = kind;
+    o.reserved = 0;
+    *r = o;
+}
+
+// ------------------------------------------------- streaming segment
+
+// One segment [b, e) of a streaming task.  Thread t of the CTA handles, in
+// each chunk of BLOCK*IPT*4 elements starting at c, the four elements
+// c + 4*(j*BLOCK + t) + {0..3} for j < IPT -- the same mapping in the vector
+// path and in the masked scalar path (ragged tail, or an unaligned
+// partition), so the fp32 grouping of a chunk never depends on the path.
+template <int BLOCK, int IPT, int KIND>
+__device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTask& t,
+                                               uint32_t task, uint32_t local, RedSmem& sm) {
+    constexpr bool F32 = (KIND == K_F32_IDENT || KIND == K_F32_POLY3);
+    constexpr uint32_t CH = BLOCK * IPT * 4;
+    const uint64_t b = (uint64_t)local * t.seg_elems;
+    const uint64_t e = min(b + (uint64_t)t.seg_elems, t.n);
+    const char* base = static_cast<const char*>(t.in0);
+    const float ca = t.coef[0], cb = t.coef[1], cc = t.coef[2];
+
+    unsigned long long usum = 0;
+    double dsum = 0.0;
+    float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+
+    uint64_t i = b;
+    if (t.flags & TF_ALIGNED) {
+        for (; i + CH <= e; i += CH) {
+            uint4 v[IPT];
+            const char* p = base + (i + (uint64_t)threadIdx.x * 4) * 4;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) v[j] = ld_stream_v4(p + (size_t)j * BLOCK * 16);
+            if constexpr (F32) {
+                float cs = 0.f;
+#pragma unroll
+                for (int j = 0; j < IPT; ++j) {
+                    const float y0 = map_f32<KIND>(__uint_as_float(v[j].x), ca, cb, cc);
+                    const float y1 = map_f32<KIND>(__uint_as_float(v[j].y), ca, cb, cc);
+                    const float y2 = map_f32<KIND>(__uint_as_float(v[j].z), ca, cb, cc);
+                    const float y3 = map_f32<KIND>(__uint_as_float(v[j].w), ca, cb, cc);
+                    cs += __fadd_rn(__fadd_rn(y0, y1), __fadd_rn(y2, y3));
+                    mn = fminf(mn, fminf(fminf(y0, y1), fminf(y2, y3)));
+                    mx = fmaxf(mx, fmaxf(fmaxf(y0, y1), fmaxf(y2, y3)));
+                }
+                dsum += (double)cs;
+            } else {
+#pragma unroll
+                for (int j = 0; j < IPT; ++j) {
+                    usum += (unsigned long long)map_u32<KIND>(v[j].x) +
+                            (unsigned long long)map_u32<KIND>(v[j].y) +
+                            (unsigned long long)map_u32<KIND>(v[j].z) +
+                            (unsigned long long)map_u32<KIND>(v[j].w);
+                }
+            }
+        }
+    }
+    // masked scalar path: the ragged tail of the segment, or every chunk of an
+    // unaligned partition
+    for (; i < e; i += CH) {
+        float cs = 0.f;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint64_t g = i + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
+            uint32_t w[4];
+            bool ok[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ok[q] = g + q < e;
+                w[q] = ok[q] ? ld_stream_b32(base + (g + q) * 4) : 0u;
+            }
+            if constexpr (F32) {
+                float y[4], ys[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    y[q] = map_f32<KIND>(__uint_as_float(w[q]), ca, cb, cc);
+                    ys[q] = ok[q] ? y[q] : 0.f;
+                    if (ok[q]) {
+                        mn = fminf(mn, y[q]);
+                        mx = fmaxf(mx, y[q]);
+                    }
+                }
+                cs += __fadd_rn(__fadd_rn(ys[0], ys[1]), __fadd_rn(ys[2], ys[3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (ok[q]) usum += (unsigned long long)map_u32<KIND>(w[q]);
+            }
+        }
+        if constexpr (F32) dsum += (double)cs;
+    }
+
+    if constexpr (F32) block_reduce_f<BLOCK>(dsum, mn, mx, sm);
+    else usum = block_sum_u64<BLOCK>(usum, sm);
+    if constexpr (!F32) dsum = (double)usum;
+
+    if (t.nseg == 1) {
+        if (threadIdx.x == 0)
+            write_result(t.result, usum, dsum, F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, t.n, t.kind);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        StreamPartial* sp = a.spart + t.slot0 + local;
+        sp->s = dsum;
+        sp->u = usum;
+        sp->mn = mn;
+        sp->mx = mx;
+        __threadfence();
+        const uint32_t prev = atomicAdd(&a.tickets[task], 1u);
+        sm.flag = (prev == t.nseg - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (sm.flag == 0) return;   // uniform across the CTA
+    __threadfence();
+
+    // This CTA finished the task's last segment: fold the partials in slot order.
+    double fs = 0.0;
+    unsigned long long fu = 0;
+    float fmn = CUDART_INF_F, fmx = -CUDART_INF_F;
+    for (uint32_t s = threadIdx.x; s < t.nseg; s += BLOCK) {
+        const StreamPartial* sp = a.spart + t.slot0 + s;
+        if constexpr (F32) {
+            fs += __ldcg(&sp->s);
+            fmn = fminf(fmn, __ldcg(&sp->mn));
+            fmx = fmaxf(fmx, __ldcg(&sp->mx));
+        } else {
+            fu += __ldcg(reinterpret_cast<const unsigned long long*>(&sp->u));
+        }
+    }
+    if constexpr (F32) block_reduce_f<BLOCK>(fs, fmn, fmx, sm);
+    else {
+        fu = block_sum_u64<BLOCK>(fu, sm);
+        fs = (double)fu;
+    }
+    if (threadIdx.x == 0) {
+        write_result(t.result, fu, fs, F32 ? fmn : 0.f, F32 ? fmx : 0.f, SCL_OK, t.n, t.kind);
+        a.tickets[task] = 0u;   // ready for the next launch
+    }
+}
+
+// ------------------------------------------------------------ keyed piece
+
+__device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, uint32_t* cnt,
+                                          float* sum, uint32_t& bad) {
+    if (k < nk) {           // a negative int32 key is a huge uint32: rejected here
+        atomicAdd(&cnt[k], 1u);
+        atomicAdd(&sum[k], __uint_as_float(v));
+    } else {
+        bad = 1u;
+    }
+}
+
+// One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
+// shared-memory table (count, fp32 sum) and written to the outputs (single
+// piece) or to partial slot slot0 + slot.
+template <int BLOCK, int IPT>
+__device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
+                                            uint32_t slot, uint64_t b, uint64_t e,
+                                            uint32_t* tab, RedSmem& sm) {
+    constexpr uint32_t CH = BLOCK * IPT * 4;
+    uint32_t* cnt = tab;
+    float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
+    const uint32_t nk = t.num_keys;
+    for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+        cnt[k] = 0u;
+        sum[k] = 0.f;
+    }
+    __syncthreads();
+
+    const char* kb = static_cast<const char*>(t.in0);
+    const char* vb = static_cast<const char*>(t.in1);
+    uint32_t bad = 0;
+    uint64_t i = b;
+    if (t.flags & TF_ALIGNED) {
+        for (; i + CH <= e; i += CH) {
+            uint4 kv[IPT], vv[IPT];
+            const uint64_t off = (i + (uint64_t)threadIdx.x * 4) * 4;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) kv[j] = ld_stream_v4(kb + off + (size_t)j * BLOCK * 16);
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) vv[j] = ld_stream_v4(vb + off + (size_t)j * BLOCK * 16);
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                keyed_add(kv[j].x, vv[j].x, nk, cnt, sum, bad);
+                keyed_add(kv[j].y, vv[j].y, nk, cnt, sum, bad);
+                keyed_add(kv[j].z, vv[j].z, nk, cnt, sum, bad);
+                keyed_add(kv[j].w, vv[j].w, nk, cnt, sum, bad);
+            }
+        }
+    }
+    for (; i < e; i += CH) {
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint64_t g = i + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (g + q < e)
+                    keyed_add(ld_stream_b32(kb + (g + q) * 4), ld_stream_b32(vb + (g + q) * 4), nk,
+                              cnt, sum, bad);
+        }
+    }
+    const int any_bad = __syncthreads_or((int)bad);
+
+    if (t.nseg == 1) {
+        unsigned long long ctot = 0;
+        double stot = 0.0;
+        for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+            const uint32_t c = cnt[k];
+            const float s = sum[k];
+            t.counts_out[k] = c;
+            t.sums_out[k] = s;
+            if (t.sums64_out) t.sums64_out[k] = (double)s;
+            ctot += c;
+            stot += (double)s;
+        }
+        float dummy0 = CUDART_INF_F, dummy1 = -CUDART_INF_F;
+        block_reduce_f<BLOCK>(stot, dummy0, dummy1, sm);
+        ctot = block_sum_u64<BLOCK>(ctot, sm);
+        if (threadIdx.x == 0)
+            write_result(t.result, ctot, stot, CUDART_INF_F, -CUDART_INF_F,
+                         any_bad ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
+    } else {
+        uint32_t* dst = a.kpart + (size_t)(t.slot0 + slot) * kKeyedTableWords;
+        for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+            __stcg(dst + k, cnt[k]);
+            __stcg(dst + kMaxKeys + k, __float_as_uint(sum[k]));
+        }
+        if (any_bad && threadIdx.x == 0) atomicOr(&a.task_flags[task], 1u);
+    }
+    __syncthreads();   // the table is re-zeroed by the next piece
+}
+
+// ------------------------------------------------------- persistent kernel
+
+template <int BLOCK, int IPT, int MASK>
+__global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ KernelArgs a) {
+    __shared__ RedSmem sm;
+    extern __shared__ uint4 dyn_smem[];
+
+    if constexpr (mask_has_keyed(MASK)) {
+        uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
+        if (a.tasks == nullptr) {
+            if (a.single.kind == K_KEYED && blockIdx.x < a.nkeyed_ctas) {
+                const uint32_t G = a.nkeyed_ctas;
+                keyed_piece<BLOCK, IPT>(a, a.single, 0u, blockIdx.x,
+                                        keyed_single_bound(a.single.n, blockIdx.x, G),
+                                        keyed_single_bound(a.single.n, blockIdx.x + 1, G), tab, sm);
+            }
+        } else {
+            const uint32_t p0 = a.kp_first[blockIdx.x], p1 = a.kp_first[blockIdx.x + 1];
+            for (uint32_t p = p0; p < p1; ++p) {
+                const KPiece kp = a.kpieces[p];
+                const DevTask t = a.tasks[kp.task];
+                keyed_piece<BLOCK, IPT>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+            }
+        }
+    }
+
+    if constexpr (mask_has_stream(MASK)) {
+        if (a.nseg_stream > 0) {
+            if (threadIdx.x == 0) sm.q = atomicAdd(&a.hdr[H_QUEUE], 1u);
+            __syncthreads();
+            uint32_t q = sm.q;
+            while (q < a.nseg_stream) {
+                __syncthreads();   // everyone has read sm.q
+                if (threadIdx.x == 0) sm.q = atomicAdd(&a.hdr[H_QUEUE], 1u);
+                const uint32_t task = a.tasks ? a.seg_task[q] : 0u;
+                const DevTask t = a.tasks ? a.tasks[task] : a.single;
+                const uint32_t local = q - t.seg_base;
+                bool done = false;
+                if constexpr (mask_has_u32(MASK)) {
+                    if (t.kind == K_U32_IDENT) {
+                        stream_segment<BLOCK, IPT, K_U32_IDENT>(a, t, task, local, sm);
+                        done = true;
+                    } else if (t.kind == K_U32_MIX32) {
+                        stream_segment<BLOCK, IPT, K_U32_MIX32>(a, t, task, local, sm);
+                        done = true;
+                    }
+                }
+                if constexpr (mask_has_f32(MASK)) {
+                    if (!done && t.kind == K_F32_IDENT) {
+                        stream_segment<BLOCK, IPT, K_F32_IDENT>(a, t, task, local, sm);
+                        done = true;
+                    } else if (!done && t.kind == K_F32_POLY3) {
+                        stream_segment<BLOCK, IPT, K_F32_POLY3>(a, t, task, local, sm);
+                        done = true;
+                    }
+                }
+                if (!done) {   // a kind this instantiation does not contain: host bug
+                    if (threadIdx.x == 0) atomicOr(&a.hdr[H_ERROR], 1u);
+                    __syncthreads();
+                }
+                q = sm.q;   // written by thread 0 before the segment's barriers
+            }
+        }
+    }
+
+    // Last CTA out rewinds the segment counter for the next launch.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(&a.hdr[H_EXIT], 1u);
+        if (done == gridDim.x - 1) {
+            atomicExch(&a.hdr[H_QUEUE], 0u);
+            atomicExch(&a.hdr[H_EXIT], 0u);
+        }
+    }
+}
+
+// --------------------------------------------------------- keyed fold pass
+
+// grid (key blocks, fold tasks).  Each thread folds one key over the task's
+// piece tables in piece order: count exact in uint32, sum in fp64.
+template <int FB>
+__global__ void __launch_bounds__(FB) k_keyed_fold(const __grid_constant__ KernelArgs a) {
+    static_assert(FB == kFoldBlock, "fold block");
+    __shared__ RedSmem sm;
+    const uint32_t fi = blockIdx.y;
+    const uint32_t task = a.tasks ? a.fold_tasks[fi] : 0u;
+    const DevTask t = a.tasks ? a.tasks[task] : a.single;
+    const uint32_t nk = t.num_keys;
+    const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;
+    if (blockIdx.x >= nkb) return;   // uniform: this task has fewer key blocks
+
+    const uint32_t k = blockIdx.x * kFoldBlock + threadIdx.x;
+    unsigned long long ctot = 0;
+    double stot = 0.0;
+    if (k < nk) {
+        const uint32_t* src = a.kpart + (size_t)t.slot0 * kKeyedTableWords + k;
+        const uint32_t np = t.nseg;
+        uint32_t c = 0;
+        double s = 0.0;
+        uint32_t p = 0;
+        for (; p + 4 <= np; p += 4) {
+            uint32_t cc[4], sv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cc[q] = __ldcg(src + (size_t)(p + q) * kKeyedTableWords);
+                sv[q] = __ldcg(src + (size_t)(p + q) * kKeyedTableWords + kMaxKeys);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                c += cc[q];
+                s += (double)__uint_as_float(sv[q]);
+            }
+        }
+        for (; p < np; ++p) {
+            c += __ldcg(src + (size_t)p * kKeyedTableWords);
+            s += (double)__uint_as_float(__ldcg(src + (size_t)p * kKeyedTableWords + kMaxKeys));
+        }
+        t.counts_out[k] = c;
+        t.sums_out[k] = (float)s;
+        if (t.sums64_out) t.sums64_out[k] = s;
+        ctot = c;
+        stot = s;
+    }
+    float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
+    block_reduce_f<kFoldBlock>(stot, d0, d1, sm);
+    ctot = block_sum_u64<kFoldBlock>(ctot, sm);
+    if (threadIdx.x == 0) {
+        StreamPartial* fp = a.fpart + (size_t)fi * (kMaxKeys / kFoldBlock) + blockIdx.x;
+        fp->s = stot;
+        fp->u = ctot;
+        __threadfence();
+        const uint32_t prev = atomicAdd(&a.tickets[task], 1u);
+        if (prev == nkb - 1) {
+            __threadfence();
+            double s = 0.0;
+            unsigned long long c = 0;
+            for (uint32_t kb = 0; kb < nkb; ++kb) {
+                const StreamPartial* q = a.fpart + (size_t)fi * (kMaxKeys / kFoldBlock) + kb;
+                s += __ldcg(&q->s);
+                c += __ldcg(reinterpret_cast<const unsigned long long*>(&q->u));
+            }
+            const uint32_t fl = atomicExch(&a.task_flags[task], 0u);
+            write_result(t.result, c, s, CUDART_INF_F, -CUDART_INF_F,
+                         fl ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
+            a.tickets[task] = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------- map kernel
+
+template <int BLOCK, int IPT, int KIND, bool ALIGNED>
+__global__ void __launch_bounds__(BLOCK) k_map(const void* in, void* out, uint64_t n, float ca,
+                                               float cb, float cc) {
+    constexpr uint32_t CH = BLOCK * IPT * 4;
+    const char* ib = static_cast<const char*>(in);
+    char* ob = static_cast<char*>(out);
+    const uint64_t nch = ALIGNED ? n / CH : 0;
+    for (uint64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint64_t off = (c * CH + (uint64_t)threadIdx.x * 4) * 4;
+        uint4 v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) v[j] = ld_stream_v4(ib + off + (size_t)j * BLOCK * 16);
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            uint4 r;
+            if constexpr (KIND == K_F32_POLY3) {
+                r.x = __float_as_uint(poly3(__uint_as_float(v[j].x), ca, cb, cc));
+                r.y = __float_as_uint(poly3(__uint_as_float(v[j].y), ca, cb, cc));
+                r.z = __float_as_uint(poly3(__uint_as_float(v[j].z), ca, cb, cc));
+                r.w = __float_as_uint(poly3(__uint_as_float(v[j].w), ca, cb, cc));
+            } else {
+                r.x = map_u32<KIND>(v[j].x);
+                r.y = map_u32<KIND>(v[j].y);
+                r.z = map_u32<KIND>(v[j].z);
+                r.w = map_u32<KIND>(v[j].w);
+            }
+            st_stream_v4(ob + off + (size_t)j * BLOCK * 16, r);
+        }
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * BLOCK;
+    for (uint64_t i = nch * CH + (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += stride) {
+        const uint32_t w = ld_stream_b32(ib + i * 4);
+        uint32_t r;
+        if constexpr (KIND == K_F32_POLY3) r = __float_as_uint(poly3(__uint_as_float(w), ca, cb, cc));
+        else r = map_u32<KIND>(w);
+        reinterpret_cast<uint32_t*>(ob)[i] = r;
+    }
+}
+
+}  // namespace dev
+}  // namespace scl
+
+// Instantiate the persistent kernel for one mask over the tuned shapes and
+// define kernel_table_<name>().
+#define SCL_DYN(M) (scl::mask_has_keyed(M) ? scl::kKeyedSmemBytes : 0)
+#define SCL_SHAPE(M, B, I) {M, B, I, (const void*)&scl::dev::k_persistent<B, I, M>, SCL_DYN(M)}
+#define SCL_DEFINE_TABLE(NAME, M)                                                   \
+    namespace scl {                                                                 \
+    const KernelEntry* kernel_table_##NAME(int* count) {                            \
+        static const KernelEntry tab[] = {SCL_SHAPE(M, 256, 2), SCL_SHAPE(M, 256, 4), \
+                                          SCL_SHAPE(M, 256, 8), SCL_SHAPE(M, 512, 2), \
+                                          SCL_SHAPE(M, 512, 4), SCL_SHAPE(M, 512, 8)}; \
+        *count = (int)(sizeof(tab) / sizeof(tab[0]));                               \
+        return tab;                                                                 \
+    }                                                                               \
+    }

@@ -1,0 +1,567 @@
+// runtime.cu -- host runtime of libscl: errors, arena, kernel lookup, the
+// single-partition launch and the batch planner.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <fstream>
+#include <sstream>
+
+#include "runtime.h"
+
+namespace scl {
+
+const KernelEntry* kernel_table_u32(int* count);
+const KernelEntry* kernel_table_f32(int* count);
+const KernelEntry* kernel_table_keyed(int* count);
+const KernelEntry* kernel_table_all(int* count);
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+void clear_error() { t_err.clear(); }
+const char* last_error() { return t_err.c_str(); }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------- arena
+
+void Arena::init(char* base, size_t size) {
+    std::lock_guard<std::mutex> g(mu_);
+    base_ = base;
+    size_ = size / kAlign * kAlign;
+    free_.clear();
+    used_.clear();
+    if (size_) free_[0] = size_;
+}
+
+void* Arena::alloc(size_t bytes) {
+    bytes = align_up(bytes ? bytes : 1);
+    std::lock_guard<std::mutex> g(mu_);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second < bytes) continue;
+        const size_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        used_[off] = bytes;
+        return base_ + off;
+    }
+    return nullptr;
+}
+
+void Arena::release(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(mu_);
+    const size_t off = (size_t)((char*)p - base_);
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t start = off, sz = u->second;
+    used_.erase(u);
+    auto nx = free_.lower_bound(start);
+    if (nx != free_.end() && nx->first == start + sz) {
+        sz += nx->second;
+        nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == start) {
+            start = pv->first;
+            sz += pv->second;
+            free_.erase(pv);
+        }
+    }
+    free_[start] = sz;
+}
+
+size_t Arena::free_bytes() {
+    std::lock_guard<std::mutex> g(mu_);
+    size_t s = 0;
+    for (auto& kv : free_) s += kv.second;
+    return s;
+}
+
+size_t Arena::largest_free() {
+    std::lock_guard<std::mutex> g(mu_);
+    size_t s = 0;
+    for (auto& kv : free_) s = std::max(s, kv.second);
+    return s;
+}
+
+// ----------------------------------------------------------- kernel lookup
+
+static const KernelEntry* table(int mask, int* count) {
+    switch (mask) {
+        case M_U32: return kernel_table_u32(count);
+        case M_F32: return kernel_table_f32(count);
+        case M_KEYED: return kernel_table_keyed(count);
+        default: return kernel_table_all(count);
+    }
+}
+
+const KernelEntry* find_entry(int mask, int block, int ipt) {
+    int n = 0;
+    const KernelEntry* t = table(mask, &n);
+    for (int i = 0; i < n; ++i)
+        if (t[i].block == block && t[i].ipt == ipt) return &t[i];
+    return nullptr;
+}
+
+int mask_of_kind(uint32_t kind) {
+    switch (kind) {
+        case K_U32_IDENT:
+        case K_U32_MIX32: return M_U32;
+        case K_F32_IDENT:
+        case K_F32_POLY3: return M_F32;
+        default: return M_KEYED;
+    }
+}
+
+int resolve_kind(scl_dtype dt, int kernel, int reduce, uint32_t* kind) {
+    switch (dt) {
+        case SCL_U32:
+        case SCL_I32:
+            if (reduce != SCL_R_SUM) break;
+            if (kernel == SCL_K_IDENT) { *kind = K_U32_IDENT; return SCL_OK; }
+            if (kernel == SCL_K_MIX32) { *kind = K_U32_MIX32; return SCL_OK; }
+            break;
+        case SCL_F32:
+            if (reduce != SCL_R_SUM && reduce != SCL_R_SUM_MIN_MAX) break;
+            if (kernel == SCL_K_IDENT) { *kind = K_F32_IDENT; return SCL_OK; }
+            if (kernel == SCL_K_POLY3) { *kind = K_F32_POLY3; return SCL_OK; }
+            break;
+        case SCL_KV_I32_F32:
+            if (reduce == SCL_R_KEYED_COUNT_SUM && kernel == SCL_K_IDENT) {
+                *kind = K_KEYED;
+                return SCL_OK;
+            }
+            break;
+        default:
+            return fail(SCL_E_INVALID, "unknown dtype %d", (int)dt);
+    }
+    return fail(SCL_E_UNSUPPORTED, "no catalogue kernel for dtype %d, map %d, reduce %d",
+                (int)dt, kernel, reduce);
+}
+
+// ------------------------------------------------------------ launch shape
+
+// F32 tasks must see the same (block, items-per-thread) whether they run
+// alone or inside a mixed batch, so the mixed kernel borrows the fp32 shape.
+Shape Ctx::shape_for(int mask) const {
+    Shape s = shape[mask];
+    if (mask == M_ALL) {
+        s.block = shape[M_F32].block;
+        s.ipt = shape[M_F32].ipt;
+    }
+    return s;
+}
+
+uint32_t Ctx::grid_max(int mask, const Shape& sh) {
+    const KernelEntry* e = find_entry(mask, sh.block, sh.ipt);
+    if (!e) return 1;
+    auto key = std::make_pair(e->fn, 0);
+    int nb = 0;
+    auto it = occ_cache.find(key);
+    if (it != occ_cache.end()) {
+        nb = it->second;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e->fn, sh.block, e->dyn_smem) !=
+            cudaSuccess)
+            nb = 1;
+        if (nb < 1) nb = 1;
+        occ_cache[key] = nb;
+    }
+    const int per = sh.ctas_per_sm > 0 ? std::min(sh.ctas_per_sm, nb) : nb;
+    return (uint32_t)(sms * per);
+}
+
+// ----------------------------------------------------------------- scratch
+
+static int grow(Ctx* c, void** p, size_t* cap, size_t need, size_t elem, bool zero,
+                std::vector<void*>& blocks) {
+    if (*cap >= need && *p) return SCL_OK;
+    size_t n = std::max<size_t>(need, 64);
+    size_t pow2 = 64;
+    while (pow2 < n) pow2 <<= 1;
+    // Work already enqueued may still read the old block.
+    SCL_CUDA(cudaDeviceSynchronize());
+    if (*p) {
+        blocks.erase(std::remove(blocks.begin(), blocks.end(), *p), blocks.end());
+        c->arena.release(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    void* q = c->arena.alloc(pow2 * elem);
+    if (!q) return fail(SCL_E_NOMEM, "arena: no block of %zu bytes for scratch", pow2 * elem);
+    if (zero) SCL_CUDA(cudaMemset(q, 0, pow2 * elem));
+    blocks.push_back(q);
+    *p = q;
+    *cap = pow2;
+    return SCL_OK;
+}
+
+int ensure_scratch(Ctx* c, Scratch* s, size_t tasks, size_t sslots, size_t kslots,
+                   size_t fparts) {
+    if (!s->hdr) {
+        void* h = c->arena.alloc(H_WORDS * 4);
+        if (!h) return fail(SCL_E_NOMEM, "arena: no room for scratch header");
+        SCL_CUDA(cudaMemset(h, 0, H_WORDS * 4));
+        s->hdr = (uint32_t*)h;
+        s->blocks.push_back(h);
+    }
+    if (s->task_cap < tasks || !s->tickets) {
+        size_t cap = s->task_cap;
+        void* t = s->tickets;
+        SCL_TRY(grow(c, &t, &cap, tasks, 4, true, s->blocks));
+        size_t cap2 = s->task_cap;
+        void* f = s->flags;
+        SCL_TRY(grow(c, &f, &cap2, tasks, 4, true, s->blocks));
+        s->tickets = (uint32_t*)t;
+        s->flags = (uint32_t*)f;
+        s->task_cap = std::min(cap, cap2);
+    }
+    if (sslots) {
+        void* p = s->spart;
+        SCL_TRY(grow(c, &p, &s->spart_cap, sslots, sizeof(StreamPartial), false, s->blocks));
+        s->spart = (StreamPartial*)p;
+    }
+    if (kslots) {
+        void* p = s->kpart;
+        SCL_TRY(grow(c, &p, &s->kpart_cap, kslots, (size_t)kKeyedTableWords * 4, false, s->blocks));
+        s->kpart = (uint32_t*)p;
+    }
+    if (fparts) {
+        void* p = s->fpart;
+        SCL_TRY(grow(c, &p, &s->fpart_cap, fparts, sizeof(StreamPartial), false, s->blocks));
+        s->fpart = (StreamPartial*)p;
+    }
+    return SCL_OK;
+}
+
+void fill_task(DevTask* t, const Partition& p, uint32_t kind, const float* coef, uint32_t nk) {
+    memset(t, 0, sizeof *t);
+    t->in0 = p.d0;
+    t->in1 = p.d1;
+    t->n = p.n;
+    t->kind = kind;
+    t->num_keys = nk;
+    static const float kDef[3] = {0.5f, -1.25f, 0.1f};
+    const float* cf = coef ? coef : kDef;
+    t->coef[0] = cf[0];
+    t->coef[1] = cf[1];
+    t->coef[2] = cf[2];
+    const bool al = ((uintptr_t)p.d0 % 16 == 0) && (!p.d1 || (uintptr_t)p.d1 % 16 == 0);
+    t->flags = al ? TF_ALIGNED : 0u;
+}
+
+// --------------------------------------------------------- single launches
+
+static int launch_kernel(const void* fn, uint32_t grid, uint32_t block, size_t smem,
+                         const KernelArgs& args, cudaStream_t st) {
+    void* params[] = {const_cast<KernelArgs*>(&args)};
+    SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, st));
+    count_launches(1);
+    return SCL_OK;
+}
+
+int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uint32_t nk,
+               uint32_t* counts, float* sums, double* sums64, scl_result* dres,
+               cudaStream_t st) {
+    const int mask = mask_of_kind(kind);
+    const Shape sh = c->shape_for(mask);
+    const KernelEntry* e = find_entry(mask, sh.block, sh.ipt);
+    if (!e) return fail(SCL_E_STATE, "no kernel for shape %d x %d", sh.block, sh.ipt);
+    const uint32_t gmax = c->grid_max(mask, sh);
+
+    KernelArgs a;
+    memset(&a, 0, sizeof a);
+    fill_task(&a.single, p, kind, coef, nk);
+    DevTask& t = a.single;
+    t.result = dres;
+    t.counts_out = counts;
+    t.sums_out = sums;
+    t.sums64_out = sums64;
+    uint32_t grid;
+    if (kind == K_KEYED) {
+        const uint32_t G = keyed_single_pieces(p.n, gmax);
+        t.nseg = G;
+        a.nkeyed_ctas = G;
+        grid = G;
+        SCL_TRY(ensure_scratch(c, &c->single, 1, 0, G > 1 ? G : 0, kMaxKeys / kFoldBlock));
+    } else {
+        const uint32_t chunk = (uint32_t)(sh.block * sh.ipt * 4);
+        t.seg_elems = stream_seg_elems(p.n, chunk);
+        t.nseg = stream_nseg(p.n, t.seg_elems);
+        a.nseg_stream = t.nseg;
+        grid = std::min(gmax, t.nseg);
+        SCL_TRY(ensure_scratch(c, &c->single, 1, t.nseg, 0, 0));
+    }
+    a.spart = c->single.spart;
+    a.kpart = c->single.kpart;
+    a.fpart = c->single.fpart;
+    a.tickets = c->single.tickets;
+    a.task_flags = c->single.flags;
+    a.hdr = c->single.hdr;
+    SCL_TRY(launch_kernel(e->fn, grid, sh.block, e->dyn_smem, a, st));
+    if (kind == K_KEYED && t.nseg > 1) {
+        const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;
+        void* params[] = {&a};
+        SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(nkb, 1), dim3(kFoldBlock), params, 0, st));
+        count_launches(1);
+    }
+    return SCL_OK;
+}
+
+// ----------------------------------------------------------------- planner
+
+int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
+    P->tasks.assign(nt, DevTask{});
+    bool has_u32 = false, has_f32 = false, has_keyed = false;
+    std::vector<uint32_t> kind(nt);
+    for (uint32_t i = 0; i < nt; ++i) {
+        const Partition* p = c->part(in[i].part);
+        if (!p) return fail(SCL_E_INVALID, "task %u: unknown partition handle %llu", i,
+                            (unsigned long long)in[i].part);
+        SCL_TRY(resolve_kind(p->dtype, in[i].kernel, in[i].reduce, &kind[i]));
+        uint32_t nk = 0;
+        if (kind[i] == K_KEYED) {
+            nk = in[i].num_keys;
+            if (nk < 1 || nk > kMaxKeys)
+                return fail(SCL_E_INVALID, "task %u: num_keys %u not in [1, %u]", i, nk, kMaxKeys);
+            if (!in[i].counts_out || !in[i].sums_out)
+                return fail(SCL_E_INVALID, "task %u: keyed task needs counts_out and sums_out", i);
+        }
+        fill_task(&P->tasks[i], *p, kind[i], in[i].coef, nk);
+        DevTask& t = P->tasks[i];
+        t.counts_out = in[i].counts_out;
+        t.sums_out = in[i].sums_out;
+        t.sums64_out = in[i].sums64_out;
+        has_u32 |= mask_of_kind(kind[i]) == M_U32;
+        has_f32 |= mask_of_kind(kind[i]) == M_F32;
+        has_keyed |= kind[i] == K_KEYED;
+    }
+    const int ntypes = (int)has_u32 + (int)has_f32 + (int)has_keyed;
+    P->mask = ntypes > 1 ? M_ALL : has_keyed ? M_KEYED : has_f32 ? M_F32 : M_U32;
+    P->shape = c->shape_for(P->mask);
+    if (!find_entry(P->mask, P->shape.block, P->shape.ipt))
+        return fail(SCL_E_STATE, "no kernel for shape %d x %d", P->shape.block, P->shape.ipt);
+    const uint32_t gmax = c->grid_max(P->mask, P->shape);
+    const uint32_t chunk = (uint32_t)(P->shape.block * P->shape.ipt * 4);
+
+    // streaming segments: task-relative, length fixed by n and the shape
+    P->seg_task.clear();
+    P->nseg_stream = 0;
+    P->sslots = 0;
+    uint64_t W = 0;   // keyed cost
+    for (uint32_t i = 0; i < nt; ++i) {
+        DevTask& t = P->tasks[i];
+        if (kind[i] == K_KEYED) {
+            W += t.n + kKeyedTaskOverhead;
+            continue;
+        }
+        t.seg_elems = stream_seg_elems(t.n, chunk);
+        t.nseg = stream_nseg(t.n, t.seg_elems);
+        t.slot0 = P->sslots;
+        t.seg_base = P->nseg_stream;
+        P->sslots += t.nseg;
+        P->nseg_stream += t.nseg;
+        P->seg_task.insert(P->seg_task.end(), t.nseg, i);
+    }
+
+    // keyed pieces: an even share of the keyed cost per CTA, cut at 64-pair
+    // boundaries, in CTA order
+    uint32_t Gk = 0;
+    if (has_keyed) {
+        uint64_t g = (W + kKeyedMinPiece - 1) / kKeyedMinPiece;
+        Gk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(g, gmax));
+    }
+    uint32_t grid = std::max<uint32_t>(Gk, std::min<uint32_t>(gmax, P->nseg_stream));
+    P->grid = std::max<uint32_t>(grid, 1);
+    P->kp_first.assign(P->grid + 1, 0);
+    P->kpieces.clear();
+    P->fold_tasks.clear();
+    P->kslots = 0;
+    if (has_keyed) {
+        auto R = [&](uint64_t cta) -> uint64_t {
+            return (uint64_t)((unsigned __int128)cta * W / Gk);
+        };
+        std::vector<uint32_t> cta_of_piece;
+        uint64_t A = 0;
+        for (uint32_t i = 0; i < nt; ++i) {
+            if (kind[i] != K_KEYED) continue;
+            DevTask& t = P->tasks[i];
+            const uint64_t cost = t.n + kKeyedTaskOverhead, B = A + cost;
+            uint32_t c0 = (uint32_t)((unsigned __int128)A * Gk / W);
+            while (c0 + 1 < Gk && R(c0 + 1) <= A) ++c0;
+            while (c0 > 0 && R(c0) > A) --c0;
+            auto emap = [&](uint64_t w) -> uint64_t {
+                if (w >= B) return t.n;
+                uint64_t e = (uint64_t)((unsigned __int128)(w - A) * t.n / cost);
+                return e / kKeyedPieceAlign * kKeyedPieceAlign;
+            };
+            uint32_t slot = 0;
+            for (uint32_t cta = c0; cta < Gk && R(cta) < B; ++cta) {
+                const uint64_t lo = std::max(A, R(cta));
+                const uint64_t hi = std::min(B, cta + 1 == Gk ? W : R(cta + 1));
+                if (lo >= hi) continue;
+                const uint64_t e0 = emap(lo), e1 = emap(hi);
+                if (e0 >= e1) continue;
+                P->kpieces.push_back(KPiece{e0, e1, i, slot++});
+                cta_of_piece.push_back(cta);
+            }
+            if (slot == 0) {   // empty or tiny task: one (possibly empty) piece
+                P->kpieces.push_back(KPiece{0, t.n, i, 0});
+                cta_of_piece.push_back(c0);
+                slot = 1;
+            }
+            t.nseg = slot;
+            t.slot0 = P->kslots;
+            if (slot > 1) {
+                P->kslots += slot;
+                P->fold_tasks.push_back(i);
+            }
+            A = B;
+        }
+        // pieces were produced in non-decreasing CTA order
+        for (size_t k = 0; k < cta_of_piece.size(); ++k) P->kp_first[cta_of_piece[k] + 1]++;
+        for (uint32_t g = 0; g < P->grid; ++g) P->kp_first[g + 1] += P->kp_first[g];
+    }
+    P->fold_gridx = P->fold_tasks.empty() ? 0 : (kMaxKeys + kFoldBlock - 1) / kFoldBlock;
+    return SCL_OK;
+}
+
+template <typename T>
+static T* carve(char* base, size_t* off, size_t count) {
+    T* p = reinterpret_cast<T*>(base + *off);
+    *off = align_up(*off + count * sizeof(T));
+    return p;
+}
+
+int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, KernelArgs* args) {
+    const size_t nt = p.tasks.size();
+    // sizes (offsets relative to the block)
+    size_t off = 0;
+    char* nil = nullptr;
+    auto o_tasks = off; carve<DevTask>(nil, &off, nt);
+    auto o_seg = off; carve<uint32_t>(nil, &off, p.seg_task.size());
+    auto o_kpf = off; carve<uint32_t>(nil, &off, p.kp_first.size());
+    auto o_kp = off; carve<KPiece>(nil, &off, p.kpieces.size());
+    auto o_fold = off; carve<uint32_t>(nil, &off, p.fold_tasks.size());
+    const size_t plan_bytes = off;
+    auto o_res = off; carve<scl_result>(nil, &off, nt);
+    const size_t zero_off = off;
+    auto o_hdr = off; carve<uint32_t>(nil, &off, H_WORDS);
+    auto o_tk = off; carve<uint32_t>(nil, &off, nt);
+    auto o_fl = off; carve<uint32_t>(nil, &off, nt);
+    const size_t zero_bytes = off - zero_off;
+    auto o_sp = off; carve<StreamPartial>(nil, &off, p.sslots);
+    auto o_fp = off; carve<StreamPartial>(nil, &off, p.fold_tasks.size() * (kMaxKeys / kFoldBlock));
+    auto o_kt = off; carve<uint32_t>(nil, &off, (size_t)p.kslots * kKeyedTableWords);
+    const size_t bytes = off;
+
+    char* b = (char*)c->arena.alloc(bytes);
+    if (!b) return fail(SCL_E_NOMEM, "arena: no block of %zu bytes for the batch", bytes);
+    img->block = b;
+    img->bytes = bytes;
+    img->tasks = (DevTask*)(b + o_tasks);
+    img->seg_task = (uint32_t*)(b + o_seg);
+    img->kp_first = (uint32_t*)(b + o_kpf);
+    img->kpieces = (KPiece*)(b + o_kp);
+    img->fold_tasks = (uint32_t*)(b + o_fold);
+    img->results = (scl_result*)(b + o_res);
+    img->hdr = (uint32_t*)(b + o_hdr);
+    img->tickets = (uint32_t*)(b + o_tk);
+    img->flags = (uint32_t*)(b + o_fl);
+    img->spart = (StreamPartial*)(b + o_sp);
+    img->fpart = (StreamPartial*)(b + o_fp);
+    img->kpart = (uint32_t*)(b + o_kt);
+    img->plan_bytes = plan_bytes;
+    img->zero_off = zero_off;
+    img->zero_bytes = zero_bytes;
+
+    for (size_t i = 0; i < nt; ++i) p.tasks[i].result = img->results + i;
+    host->assign(plan_bytes, 0);
+    char* h = host->data();
+    if (nt) memcpy(h + o_tasks, p.tasks.data(), nt * sizeof(DevTask));
+    if (!p.seg_task.empty()) memcpy(h + o_seg, p.seg_task.data(), p.seg_task.size() * 4);
+    if (!p.kp_first.empty()) memcpy(h + o_kpf, p.kp_first.data(), p.kp_first.size() * 4);
+    if (!p.kpieces.empty()) memcpy(h + o_kp, p.kpieces.data(), p.kpieces.size() * sizeof(KPiece));
+    if (!p.fold_tasks.empty()) memcpy(h + o_fold, p.fold_tasks.data(), p.fold_tasks.size() * 4);
+
+    memset(args, 0, sizeof *args);
+    args->tasks = img->tasks;
+    args->seg_task = img->seg_task;
+    args->kp_first = img->kp_first;
+    args->kpieces = img->kpieces;
+    args->fold_tasks = img->fold_tasks;
+    args->spart = img->spart;
+    args->kpart = img->kpart;
+    args->fpart = img->fpart;
+    args->tickets = img->tickets;
+    args->task_flags = img->flags;
+    args->hdr = img->hdr;
+    args->nseg_stream = p.nseg_stream;
+    args->nfold = (uint32_t)p.fold_tasks.size();
+    return SCL_OK;
+}
+
+int launch_plan(Ctx* c, const Plan& p, const KernelArgs& args, cudaStream_t st) {
+    (void)c;
+    if (p.tasks.empty()) return SCL_OK;
+    const KernelEntry* e = find_entry(p.mask, p.shape.block, p.shape.ipt);
+    if (!e) return fail(SCL_E_STATE, "no kernel for the plan's shape");
+    SCL_TRY(launch_kernel(e->fn, p.grid, p.shape.block, e->dyn_smem, args, st));
+    if (!p.fold_tasks.empty()) {
+        void* params[] = {const_cast<KernelArgs*>(&args)};
+        SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(p.fold_gridx, (uint32_t)p.fold_tasks.size()),
+                                  dim3(kFoldBlock), params, 0, st));
+        count_launches(1);
+    }
+    return SCL_OK;
+}
+
+// ------------------------------------------------------------ tuning cache
+
+static const char* kMaskNames[M_NUM] = {"u32", "f32", "keyed", "all"};
+
+int load_tuning(Ctx* c, const char* path) {
+    std::ifstream f(path);
+    if (!f) return SCL_OK;   // no cache yet
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string name;
+        int sms = 0, b = 0, ipt = 0, cps = 0;
+        if (!(is >> name >> sms >> b >> ipt >> cps)) continue;
+        if (sms != c->sms) continue;
+        for (int m = 0; m < M_NUM; ++m)
+            if (name == kMaskNames[m] && find_entry(m, b, ipt)) c->shape[m] = Shape{b, ipt, cps};
+    }
+    return SCL_OK;
+}
+
+int save_tuning(Ctx* c, const char* path) {
+    std::ofstream f(path);
+    if (!f) return fail(SCL_E_INVALID, "cannot write tune cache %s", path);
+    f << "# mask sms block items_per_thread ctas_per_sm\n";
+    for (int m = 0; m < M_NUM; ++m)
+        f << kMaskNames[m] << " " << c->sms << " " << c->shape[m].block << " " << c->shape[m].ipt
+          << " " << c->shape[m].ctas_per_sm << "\n";
+    return SCL_OK;
+}
+
+}  // namespace scl

@@ -1,0 +1,360 @@
+"""ctypes binding of libscl (include/scl.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python
+arguments (ints, numpy arrays, torch tensors' pointers) into the C types and
+turns non-zero status codes into :class:`SclError`.  There is no fallback: if
+``_lib/libscl.so`` is missing the import fails loudly.
+
+PyTorch is used only by the caller, for device memory (the arena) and streams
+(``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libscl.so")
+
+# status codes
+SCL_OK = 0
+SCL_E_INVALID = 1
+SCL_E_NOMEM = 2
+SCL_E_BUDGET = 3
+SCL_E_KEY_RANGE = 4
+SCL_E_TIMEOUT = 5
+SCL_E_PENDING = 6
+SCL_E_CUDA = 7
+SCL_E_STATE = 8
+SCL_E_UNSUPPORTED = 9
+
+# scl_dtype
+SCL_U32, SCL_I32, SCL_F32, SCL_KV_I32_F32 = 0, 1, 2, 3
+# scl_map_kernel
+SCL_K_IDENT, SCL_K_MIX32, SCL_K_POLY3 = 0, 1, 2
+# scl_reduce
+SCL_R_NONE, SCL_R_SUM, SCL_R_SUM_MIN_MAX, SCL_R_KEYED_COUNT_SUM = 0, 1, 2, 3
+
+
+class scl_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("inflight_batches", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32), ("tune_cache_path", ctypes.c_char_p)]
+
+
+class scl_result(ctypes.Structure):
+    _fields_ = [("u64_sum", ctypes.c_uint64), ("f64_sum", ctypes.c_double),
+                ("f32_sum", ctypes.c_float), ("f32_min", ctypes.c_float),
+                ("f32_max", ctypes.c_float), ("status", ctypes.c_int32),
+                ("n", ctypes.c_uint64), ("kind", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class scl_task(ctypes.Structure):
+    _fields_ = [("part", ctypes.c_uint64), ("kernel", ctypes.c_int32),
+                ("reduce", ctypes.c_int32), ("num_keys", ctypes.c_uint32),
+                ("coef", ctypes.c_float * 3), ("counts_out", ctypes.c_void_p),
+                ("sums_out", ctypes.c_void_p), ("sums64_out", ctypes.c_void_p),
+                ("reserved", ctypes.c_uint64)]
+
+
+assert ctypes.sizeof(scl_result) == 48 and ctypes.sizeof(scl_task) == 64
+
+# Result array dtype matching scl_result, for bulk reads.
+RESULT_DTYPE = np.dtype([("u64_sum", "<u8"), ("f64_sum", "<f8"), ("f32_sum", "<f4"),
+                         ("f32_min", "<f4"), ("f32_max", "<f4"), ("status", "<i4"),
+                         ("n", "<u8"), ("kind", "<u4"), ("reserved", "<u4")])
+assert RESULT_DTYPE.itemsize == 48
+
+
+class SclError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libscl.so is not built (%s); run __graft_entry__.build() or "
+                          "python paper_1505_01120_gb300/build.py" % _LIB_PATH)
+    return ctypes.CDLL(_LIB_PATH)
+
+
+lib = _load()
+
+_P = ctypes.c_void_p
+_u64, _u32, _i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "scl_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "scl_last_error": ([], ctypes.c_char_p),
+    "scl_abi_version": ([], ctypes.c_int),
+    "scl_kernel_launches_total": ([ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_create": ([ctypes.POINTER(scl_config), _PP], ctypes.c_int),
+    "scl_destroy": ([_P], ctypes.c_int),
+    "scl_arena_stats": ([_P, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_load_partition": ([_P, _P, ctypes.c_int, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_load_partition_kv": ([_P, _P, _P, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_wrap_device": ([_P, _P, _P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_free_partition": ([_P, _u64], ctypes.c_int),
+    "scl_partition_info": ([_P, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
+                            _PP, _PP], ctypes.c_int),
+    "scl_read_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
+    "scl_map": ([_P, _u64, ctypes.c_int, _P, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_map_reduce": ([_P, _u64, ctypes.c_int, _P, ctypes.c_int, _P,
+                        ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_map_reduce_async": ([_P, _u64, ctypes.c_int, _P, ctypes.c_int, _P, _P], ctypes.c_int),
+    "scl_keyed_reduce": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
+                         ctypes.c_int),
+    "scl_keyed_reduce_async": ([_P, _u64, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "scl_combine": ([_P, _u32, ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_combine_keyed": ([_P, _P, _u32, _u32, _P, _P], ctypes.c_int),
+    "scl_batch_create": ([_P, _P, _u32, _PP], ctypes.c_int),
+    "scl_batch_launch": ([_P, _P], ctypes.c_int),
+    "scl_batch_capture": ([_P, _P], ctypes.c_int),
+    "scl_batch_results": ([_P, _P, _P], ctypes.c_int),
+    "scl_batch_kernel_launches": ([_P, ctypes.POINTER(_u32)], ctypes.c_int),
+    "scl_batch_destroy": ([_P], ctypes.c_int),
+    "scl_batch_run": ([_P, _P, _u32, _P, _P], ctypes.c_int),
+}
+
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def exported_symbols() -> list[str]:
+    """Names of every entry point this binding declares."""
+    return list(_SIGS)
+
+
+def _strerror(status: int) -> str:
+    return lib.scl_strerror(status).decode()
+
+
+def _check(status: int, allow=(SCL_OK,)) -> int:
+    if status not in allow:
+        raise SclError(status, lib.scl_last_error().decode())
+    return status
+
+
+def _ptr(x) -> int | None:
+    """Address of a numpy array, a torch tensor, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _coef(coef):
+    if coef is None:
+        return None
+    c = np.ascontiguousarray(coef, dtype=np.float32)
+    if c.size != 3:
+        raise ValueError("coef must have 3 entries")
+    return c
+
+
+# ------------------------------------------------------------------ API
+
+def scl_abi_version() -> int:
+    return lib.scl_abi_version()
+
+
+def scl_kernel_launches_total() -> int:
+    v = _u64()
+    _check(lib.scl_kernel_launches_total(ctypes.byref(v)))
+    return v.value
+
+
+def scl_create(device: int, arena_ptr: int, arena_bytes: int, hbm_budget_bytes: int = 0,
+               inflight_batches: int = 4, tune_cache_path: str | None = None) -> int:
+    cfg = scl_config(device=device, arena=arena_ptr, arena_bytes=arena_bytes,
+                     hbm_budget_bytes=hbm_budget_bytes, inflight_batches=inflight_batches,
+                     tune_cache_path=tune_cache_path.encode() if tune_cache_path else None)
+    h = ctypes.c_void_p()
+    _check(lib.scl_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def scl_destroy(ctx: int) -> None:
+    _check(lib.scl_destroy(ctx))
+
+
+def scl_arena_stats(ctx: int) -> tuple[int, int]:
+    f, l = _u64(), _u64()
+    _check(lib.scl_arena_stats(ctx, ctypes.byref(f), ctypes.byref(l)))
+    return f.value, l.value
+
+
+def scl_load_partition(ctx: int, host, dtype: int, n: int | None = None, stream: int = 0) -> int:
+    if n is None:
+        n = int(host.size if isinstance(host, np.ndarray) else host.numel())
+    out = _u64()
+    _check(lib.scl_load_partition(ctx, _ptr(host), dtype, n, stream, ctypes.byref(out)))
+    return out.value
+
+
+def scl_load_partition_kv(ctx: int, keys, vals, n: int | None = None, stream: int = 0) -> int:
+    if n is None:
+        n = int(keys.size if isinstance(keys, np.ndarray) else keys.numel())
+    out = _u64()
+    _check(lib.scl_load_partition_kv(ctx, _ptr(keys), _ptr(vals), n, stream, ctypes.byref(out)))
+    return out.value
+
+
+def scl_wrap_device(ctx: int, dev0, dev1, dtype: int, n: int) -> int:
+    out = _u64()
+    _check(lib.scl_wrap_device(ctx, _ptr(dev0), _ptr(dev1), dtype, n, ctypes.byref(out)))
+    return out.value
+
+
+def scl_free_partition(ctx: int, part: int) -> None:
+    _check(lib.scl_free_partition(ctx, part))
+
+
+def scl_partition_info(ctx: int, part: int) -> tuple[int, int, int, int | None]:
+    dt, n, d0, d1 = ctypes.c_int(), _u64(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib.scl_partition_info(ctx, part, ctypes.byref(dt), ctypes.byref(n),
+                                  ctypes.byref(d0), ctypes.byref(d1)))
+    return dt.value, n.value, d0.value, d1.value
+
+
+def scl_read_partition(ctx: int, part: int, host0, host1=None, stream: int = 0) -> None:
+    _check(lib.scl_read_partition(ctx, part, _ptr(host0), _ptr(host1), stream))
+
+
+def scl_map(ctx: int, part: int, kernel: int, coef=None, stream: int = 0) -> int:
+    c = _coef(coef)
+    out = _u64()
+    _check(lib.scl_map(ctx, part, kernel, _ptr(c), stream, ctypes.byref(out)))
+    return out.value
+
+
+def scl_map_reduce(ctx: int, part: int, kernel: int, reduce: int, coef=None,
+                   stream: int = 0) -> scl_result:
+    c = _coef(coef)
+    r = scl_result()
+    _check(lib.scl_map_reduce(ctx, part, kernel, _ptr(c), reduce, stream, ctypes.byref(r)))
+    return r
+
+
+def scl_map_reduce_async(ctx: int, part: int, kernel: int, reduce: int, dev_out, coef=None,
+                         stream: int = 0) -> None:
+    c = _coef(coef)
+    _check(lib.scl_map_reduce_async(ctx, part, kernel, _ptr(c), reduce, stream, _ptr(dev_out)))
+
+
+def scl_keyed_reduce(ctx: int, part: int, num_keys: int = 4096, stream: int = 0,
+                     want_f64: bool = True):
+    """Returns (counts uint32[num_keys], sums float32[num_keys], sums64 or None,
+    scl_result).  Raises SclError(SCL_E_KEY_RANGE) after filling the tables if
+    a key was out of range; the partial tables are on the exception as .tables."""
+    counts = np.empty(num_keys, np.uint32)
+    sums = np.empty(num_keys, np.float32)
+    s64 = np.empty(num_keys, np.float64) if want_f64 else None
+    r = scl_result()
+    st = lib.scl_keyed_reduce(ctx, part, num_keys, stream, _ptr(counts), _ptr(sums), _ptr(s64),
+                              ctypes.byref(r))
+    if st == SCL_E_KEY_RANGE:
+        err = SclError(st, lib.scl_last_error().decode())
+        err.tables = (counts, sums, s64, r)
+        raise err
+    _check(st)
+    return counts, sums, s64, r
+
+
+def scl_keyed_reduce_async(ctx: int, part: int, num_keys: int, counts_dev, sums_dev,
+                           sums64_dev=None, result_dev=None, stream: int = 0) -> None:
+    _check(lib.scl_keyed_reduce_async(ctx, part, num_keys, stream, _ptr(counts_dev),
+                                      _ptr(sums_dev), _ptr(sums64_dev), _ptr(result_dev)))
+
+
+def scl_combine(parts) -> scl_result:
+    arr = (scl_result * len(parts))(*parts)
+    out = scl_result()
+    _check(lib.scl_combine(ctypes.cast(arr, ctypes.c_void_p), len(parts), ctypes.byref(out)))
+    return out
+
+
+def scl_combine_keyed(counts: np.ndarray, sums64: np.ndarray | None):
+    counts = np.ascontiguousarray(counts, np.uint32)
+    k, nk = counts.shape
+    co = np.empty(nk, np.uint32)
+    so = None
+    if sums64 is not None:
+        sums64 = np.ascontiguousarray(sums64, np.float64)
+        so = np.empty(nk, np.float64)
+    _check(lib.scl_combine_keyed(_ptr(counts), _ptr(sums64), k, nk, _ptr(co), _ptr(so)))
+    return co, so
+
+
+def make_tasks(specs) -> ctypes.Array:
+    """specs: iterable of dicts with keys part, kernel, reduce and optionally
+    num_keys, coef, counts_out, sums_out, sums64_out (device addresses)."""
+    specs = list(specs)
+    arr = (scl_task * max(1, len(specs)))()
+    for i, s in enumerate(specs):
+        t = arr[i]
+        t.part = s["part"]
+        t.kernel = s["kernel"]
+        t.reduce = s["reduce"]
+        t.num_keys = s.get("num_keys", 0)
+        cf = s.get("coef", (0.5, -1.25, 0.1))
+        t.coef[0], t.coef[1], t.coef[2] = (float(np.float32(v)) for v in cf)
+        t.counts_out = _ptr(s.get("counts_out"))
+        t.sums_out = _ptr(s.get("sums_out"))
+        t.sums64_out = _ptr(s.get("sums64_out"))
+    return arr
+
+
+def scl_batch_create(ctx: int, tasks: ctypes.Array, ntasks: int) -> int:
+    b = ctypes.c_void_p()
+    _check(lib.scl_batch_create(ctx, ctypes.cast(tasks, ctypes.c_void_p), ntasks, ctypes.byref(b)))
+    return b.value
+
+
+def scl_batch_launch(batch: int, stream: int = 0) -> None:
+    _check(lib.scl_batch_launch(batch, stream))
+
+
+def scl_batch_capture(batch: int, stream: int) -> None:
+    _check(lib.scl_batch_capture(batch, stream))
+
+
+def scl_batch_results(batch: int, ntasks: int, stream: int = 0, allow_key_range: bool = False):
+    out = np.zeros(max(1, ntasks), dtype=RESULT_DTYPE)
+    allow = (SCL_OK, SCL_E_KEY_RANGE) if allow_key_range else (SCL_OK,)
+    _check(lib.scl_batch_results(batch, stream, out.ctypes.data), allow)
+    return out[:ntasks]
+
+
+def scl_batch_kernel_launches(batch: int) -> int:
+    v = _u32()
+    _check(lib.scl_batch_kernel_launches(batch, ctypes.byref(v)))
+    return v.value
+
+
+def scl_batch_destroy(batch: int) -> None:
+    _check(lib.scl_batch_destroy(batch))
+
+
+def scl_batch_run(ctx: int, tasks: ctypes.Array, ntasks: int, stream: int = 0,
+                  allow_key_range: bool = False):
+    out = np.zeros(max(1, ntasks), dtype=RESULT_DTYPE)
+    allow = (SCL_OK, SCL_E_KEY_RANGE) if allow_key_range else (SCL_OK,)
+    _check(lib.scl_batch_run(ctx, ctypes.cast(tasks, ctypes.c_void_p), ntasks, stream,
+                             out.ctypes.data), allow)
+    return out[:ntasks]
