@@ -1,0 +1,572 @@
+"""Benchmark of the SparkCL per-partition map/reduce path on GB300.
+
+Headline (one JSON line on stdout): mapCL+reduceCL GB/s on 64 device-resident
+partitions of 4,194,304 fp32 N(0,1) values, poly3 map fused with the
+sum/min/max reduce, all 64 partitions in one persistent launch replayed from a
+CUDA graph.  A step is that one pass over 1 GiB (algorithmic bytes: 4 per
+element; the inputs are 8x the L2, so no flush is needed between steps).
+
+Also reported on the same line:
+  roofline      the persistent kernel's algorithmic bytes / its mean launch
+                time (CUDA events on its stream) against the measured HBM copy
+                peak, plus DRAM traffic per launch from the committed ncu summary
+  e2e           the same metric through the C ABI from pinned HOST buffers:
+                each step loads the 64 partitions (H2D), runs the batch, reads
+                the results (D2H)
+  cpu_baseline  the CPU oracle, one thread, on the host cores
+  configs       the other workloads: mix32 on 1,048,576 uint32 (latency) and
+                on 256 x 1,048,576 (GB/s), keyed count+sum on 16 x 16,777,216
+                pairs, 10,000 uneven partitions batched vs one launch each,
+                and the continuous-batching server when built
+  clocks        nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+Multi-GPU: ``torchrun --nproc-per-node N bench.py --gpus N``; each rank runs
+its own 64 partitions (weak scaling, no data-path collective) and the slowest
+rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1505_01120_gb300 import synth  # noqa: E402
+
+METRIC = "mapCL+reduceCL GB/s (% of HBM peak); served tasks/s and p50/p99 latency"
+PARTS, PART_N = 64, 4_194_304
+STEP_BYTES = PARTS * PART_N * 4
+WORKLOAD = "poly3_sum_min_max_64x4194304_f32"
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_persistent_f32_poly3_64x4194304.md")
+KERNEL_SOURCES = ["paper_1505_01120_gb300/csrc/kernels.cuh",
+                  "paper_1505_01120_gb300/csrc/internal.h"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic() -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    try:
+        text = open(PROFILE_MD).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch_full_workload:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference
+
+def cpu_oracle_poly3(host: np.ndarray, budget_s: float = 12.0):
+    """Time the CPU oracle (one thread) over partitions until all are done or
+    the budget is spent; returns (GB/s, partitions done, seconds)."""
+    import oracle
+    oracle.load()
+    done, t0 = 0, time.perf_counter()
+    for i in range(host.shape[0]):
+        oracle.reduce_f32(host[i], poly=True)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done * PART_N * 4 / dt / 1e9, done, dt
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.load()
+    rng = np.random.default_rng(2)
+    sample_parts = 4   # 64 MiB of the workload per step
+    host = synth.normal_f32(sample_parts * PART_N, rng).reshape(sample_parts, PART_N)
+    for _ in range(args.warmup):
+        oracle.reduce_f32(host[0], poly=True)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        for i in range(sample_parts):
+            oracle.reduce_f32(host[i], poly=True)
+    dt = time.perf_counter() - t0
+    gbs = args.steps * sample_parts * PART_N * 4 / dt / 1e9
+    sample = "%d of the 64 partitions (%d MiB) per step, CPU oracle, 1 thread" % (
+        sample_parts, sample_parts * PART_N * 4 >> 20)
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "partitions": PARTS, "elements_per_partition": PART_N},
+        "impl": "reference",
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+class Timer:
+    """CUDA events around each launch on one stream."""
+
+    def __init__(self, torch, stream):
+        self.torch, self.stream = torch, stream
+        self.ev = []
+
+    def start(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.ev.append([e, None])
+
+    def stop(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.ev[-1][1] = e
+
+    def mean_ms(self) -> float:
+        return float(np.mean([a.elapsed_time(b) for a, b in self.ev]))
+
+
+def time_device(torch, stream, fn, reps: int, warm: int = 3, flush=None) -> float:
+    """Median ms of fn() by CUDA events on `stream`, optional L2 flush before each."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            if flush is not None:
+                flush.add_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
+    """Configs other than the headline, each briefly measured."""
+    out = {}
+    st = stream.cuda_stream
+    import oracle
+
+    # mix32 on one 1,048,576-element partition: latency of the synchronous call
+    a = synth.mix32_partition()
+    p = scl.scl_load_partition(ctx.handle, a, scl.SCL_U32, stream=st)
+    r = scl.scl_map_reduce(ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, stream=st)
+    exact = r.u64_sum == oracle.sum_u32(a, mix=True)
+    lat = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        scl.scl_map_reduce(ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, stream=st)
+        lat.append((time.perf_counter() - t0) * 1e6)
+    dres = torch.zeros(48, dtype=torch.uint8, device="cuda")
+    kus = time_device(torch, stream, lambda: scl.scl_map_reduce_async(
+        ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, dres.data_ptr(), stream=st), 50) * 1e3
+    out["mix32_u64_sum_1x1048576"] = {
+        "bit_exact_vs_oracle": bool(exact), "sync_call_p50_us": float(np.percentile(lat, 50)),
+        "sync_call_p99_us": float(np.percentile(lat, 99)), "kernel_us": kus}
+    scl.scl_free_partition(ctx.handle, p)
+
+    # mix32 scaled: 256 x 1,048,576 in one launch (batch of 256)
+    big = torch.randint(-2**31, 2**31 - 1, (256 << 20,), dtype=torch.int32, device="cuda")
+    parts = [scl.scl_wrap_device(ctx.handle, big.data_ptr() + (i << 22), None, scl.SCL_U32,
+                                 1 << 20) for i in range(256)]
+    b = scl.scl_batch_create(ctx.handle, scl.make_tasks(
+        [dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_SUM) for q in parts]), 256)
+    scl.scl_batch_capture(b, st)
+    ms = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 20)
+    res = scl.scl_batch_results(b, 256, stream=st)
+    h0 = big[: 1 << 20].cpu().numpy().view(np.uint32)
+    out["mix32_u64_sum_256x1048576"] = {
+        "gbs": (256 << 22) / ms / 1e6, "frac_of_hbm": (256 << 22) / ms / 1e6 / pk,
+        "ms": ms, "partition0_bit_exact": int(res[0]["u64_sum"]) == oracle.sum_u32(h0)}
+    scl.scl_batch_destroy(b)
+    for q in parts:
+        scl.scl_free_partition(ctx.handle, q)
+    del big
+
+    # keyed count+sum: 16 x 16,777,216 pairs in one launch
+    m = 1 << 24
+    keys, vals = synth.keyed_partitions(16, m, seed=3)
+    dk = torch.from_numpy(keys.reshape(-1)).cuda()
+    dv = torch.from_numpy(vals.reshape(-1)).cuda()
+    outs = torch.zeros((16, 4096 * 4), dtype=torch.int32, device="cuda")
+    kparts, tasks = [], []
+    for i in range(16):
+        q = scl.scl_wrap_device(ctx.handle, dk.data_ptr() + i * m * 4, dv.data_ptr() + i * m * 4,
+                                scl.SCL_KV_I32_F32, m)
+        kparts.append(q)
+        base = outs[i].data_ptr()
+        tasks.append(dict(part=q, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                          num_keys=4096, counts_out=base, sums_out=base + 4096 * 4,
+                          sums64_out=base + 4096 * 8))
+    b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
+    scl.scl_batch_capture(b, st)
+    ms = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 20)
+    scl.scl_batch_results(b, 16, stream=st)
+    o0 = outs[0].cpu().numpy()
+    ocnt, osum, _ = oracle.keyed_count_sum(keys[0], vals[0], 4096)
+    s64 = o0[8192:].view(np.float64)
+    out["keyed_count_sum_16x16777216"] = {
+        "gbs": 16 * m * 8 / ms / 1e6, "frac_of_hbm": 16 * m * 8 / ms / 1e6 / pk, "ms": ms,
+        "pairs_per_s": 16 * m / ms * 1e3,
+        "partition0_counts_exact": bool(np.array_equal(o0[:4096].view(np.uint32), ocnt)),
+        "partition0_max_rel_err": float(np.max(np.abs(s64 - osum) / np.abs(osum)))}
+    scl.scl_batch_destroy(b)
+    for q in kparts:
+        scl.scl_free_partition(ctx.handle, q)
+    del dk, dv, outs
+
+    out["batch_10000"] = batch_config(torch, scl, ctx, stream)
+    return out
+
+
+def batch_config(torch, scl, ctx, stream) -> dict:
+    """10,000 uneven partitions: one persistent launch (graph) vs one launch each."""
+    st = stream.cuda_stream
+    specs = synth.batch_tasks()
+    d = synth.batch_data_packed(specs)
+    du = torch.from_numpy(d["u32"].view(np.int32)).cuda()
+    df = torch.from_numpy(d["f32"]).cuda()
+    dk = torch.from_numpy(d["keys"]).cuda()
+    dv = torch.from_numpy(d["vals"]).cuda()
+    nkeyed = sum(s.kind == synth.KIND_KEYED for s in specs)
+    kout = torch.zeros((max(1, nkeyed), 4096 * 2), dtype=torch.int32, device="cuda")
+    tasks, parts, ki = [], [], 0
+    nbytes = 0
+    for s, off in zip(specs, d["offset"]):
+        off = int(off)
+        if s.kind == synth.KIND_MIX32:
+            q = scl.scl_wrap_device(ctx.handle, du.data_ptr() + off * 4, None, scl.SCL_U32, s.n)
+            tasks.append(dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_SUM))
+            nbytes += 4 * s.n
+        elif s.kind == synth.KIND_POLY3:
+            q = scl.scl_wrap_device(ctx.handle, df.data_ptr() + off * 4, None, scl.SCL_F32, s.n)
+            tasks.append(dict(part=q, kernel=scl.SCL_K_POLY3, reduce=scl.SCL_R_SUM_MIN_MAX))
+            nbytes += 4 * s.n
+        else:
+            q = scl.scl_wrap_device(ctx.handle, dk.data_ptr() + off * 4, dv.data_ptr() + off * 4,
+                                    scl.SCL_KV_I32_F32, s.n)
+            base = kout[ki].data_ptr()
+            ki += 1
+            tasks.append(dict(part=q, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                              num_keys=4096, counts_out=base, sums_out=base + 4096 * 4))
+            nbytes += 8 * s.n + 4096 * 8
+        parts.append(q)
+    arr = scl.make_tasks(tasks)
+    n = len(tasks)
+    b = scl.scl_batch_create(ctx.handle, arr, n)
+    scl.scl_batch_capture(b, st)
+    ms_batch = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 10)
+    res_batch = scl.scl_batch_results(b, n, stream=st)
+
+    dres = torch.zeros(n * 48, dtype=torch.uint8, device="cuda")
+    dptr = dres.data_ptr()
+
+    def per_launch():
+        for i, t in enumerate(tasks):
+            if t["reduce"] == scl.SCL_R_KEYED_COUNT_SUM:
+                scl.scl_keyed_reduce_async(ctx.handle, t["part"], 4096, t["counts_out"],
+                                           t["sums_out"], None, dptr + 48 * i, stream=st)
+            else:
+                scl.scl_map_reduce_async(ctx.handle, t["part"], t["kernel"], t["reduce"],
+                                         dptr + 48 * i, stream=st)
+
+    ms_each = time_device(torch, stream, per_launch, 3, warm=1)
+    res_each = dres.cpu().numpy().view(scl.RESULT_DTYPE)
+    same_int = bool(np.array_equal(res_each["u64_sum"], res_batch["u64_sum"]))
+    f32 = np.array([s.kind == synth.KIND_POLY3 for s in specs])
+    same_f32 = bool(np.array_equal(res_each["f64_sum"][f32], res_batch["f64_sum"][f32]))
+
+    # the same per-partition launches captured once into a CUDA graph
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        per_launch()
+    ms_graph_each = time_device(torch, stream, g.replay, 5, warm=1)
+    scl.scl_batch_destroy(b)
+    for q in parts:
+        scl.scl_free_partition(ctx.handle, q)
+    return {"tasks": n, "algorithmic_bytes": nbytes,
+            "batched_graph_ms": ms_batch, "batched_tasks_per_s": n / ms_batch * 1e3,
+            "batched_gbs": nbytes / ms_batch / 1e6,
+            "per_launch_ms": ms_each, "per_launch_tasks_per_s": n / ms_each * 1e3,
+            "per_launch_graph_ms": ms_graph_each,
+            "speedup_vs_per_launch": ms_each / ms_batch,
+            "speedup_vs_per_launch_graph": ms_graph_each / ms_batch,
+            "batched_equals_per_launch_u64": same_int,
+            "batched_equals_per_launch_f32": same_f32}
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_1505_01120_gb300 import scl
+    from paper_1505_01120_gb300.context import Context
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pk = peaks()["hbm_gbs"]
+
+    # synthetic data: 64 partitions of N(0,1) fp32, one seed per rank
+    host = torch.empty(PARTS * PART_N, dtype=torch.float32, pin_memory=True)
+    synth.normal_f32(PARTS * PART_N, np.random.default_rng(2 + 1000 * rank), out=host.numpy())
+    hostv = host.numpy().reshape(PARTS, PART_N)
+    # --ncu-case: the same kernel on the same 1 GiB workload with a small arena
+    # and nothing else, sized for a profiler capture
+    ctx = Context((2 << 30) if args.ncu_case else (24 << 30), device=dev)
+    stream = torch.cuda.Stream()
+    st = stream.cuda_stream
+    parts = [scl.scl_load_partition(ctx.handle, hostv[i], scl.SCL_F32, stream=st)
+             for i in range(PARTS)]
+    torch.cuda.synchronize()
+    tasks = scl.make_tasks([dict(part=p, kernel=scl.SCL_K_POLY3, reduce=scl.SCL_R_SUM_MIN_MAX)
+                            for p in parts])
+    b = scl.scl_batch_create(ctx.handle, tasks, PARTS)
+    scl.scl_batch_capture(b, st)
+    launches_per_step = scl.scl_batch_kernel_launches(b)
+
+    for _ in range(args.warmup):
+        scl.scl_batch_launch(b, st)
+    torch.cuda.synchronize()
+    # parity spot check against the oracle on two sampled partitions
+    res = scl.scl_batch_results(b, PARTS, stream=st)
+    check = None
+    if rank == 0:
+        import oracle
+        errs = []
+        for i in (0, PARTS - 1):
+            s, mn, mx = oracle.reduce_f32(hostv[i], poly=True)
+            errs.append(abs(float(res[i]["f64_sum"]) - s) / abs(s))
+            assert res[i]["f32_min"] == mn and res[i]["f32_max"] == mx
+        check = {"sampled_partitions": 2, "max_rel_err_sum": max(errs),
+                 "min_max_exact": True}
+
+    timer = Timer(torch, stream)
+    before = scl.scl_kernel_launches_total()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            timer.start()
+            scl.scl_batch_launch(b, st)
+            timer.stop()
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+    launches = scl.scl_kernel_launches_total() - before
+    kernel_ms = timer.mean_ms()
+    step_ms = elapsed / args.steps * 1e3
+    if dist:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * STEP_BYTES / (step_ms * 1e-3) / 1e9
+    achieved = STEP_BYTES / (kernel_ms * 1e-3) / 1e9
+
+    if args.ncu_case:
+        scl.scl_batch_destroy(b)
+        log("ncu case done: %.3f ms per launch" % kernel_ms)
+        ctx.close()
+        return
+
+    # end to end through the C ABI from pinned host buffers
+    scl.scl_batch_destroy(b)
+    for p in parts:
+        scl.scl_free_partition(ctx.handle, p)
+    e2e_steps = max(2, min(args.steps, 8))
+
+    def e2e_step():
+        ps = [scl.scl_load_partition(ctx.handle, hostv[i], scl.SCL_F32, stream=st)
+              for i in range(PARTS)]
+        tk = scl.make_tasks([dict(part=p, kernel=scl.SCL_K_POLY3,
+                                  reduce=scl.SCL_R_SUM_MIN_MAX) for p in ps])
+        r = scl.scl_batch_run(ctx.handle, tk, PARTS, stream=st)
+        for p in ps:
+            scl.scl_free_partition(ctx.handle, p)
+        return r
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * STEP_BYTES / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": STEP_BYTES, "d2h_bytes_per_step": PARTS * 48,
+           "ms_per_step": e2e_ms}
+
+    configs, cpu = None, None
+    if rank == 0 and world == 1:
+        gbs, done, secs = cpu_oracle_poly3(hostv)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of the 64 partitions (%d MiB), one pass, 1 thread, %.1f s"
+                         % (done, done * PART_N * 4 >> 20, secs)}
+        if not args.no_extras:
+            configs = extra_configs(torch, scl, ctx, stream, pk, args.full)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "partitions": PARTS,
+                       "elements_per_partition": PART_N, "bytes_per_step": STEP_BYTES,
+                       "map": "poly3 y=fma(fma(0.5,x*x,-1.25),x,0.1)",
+                       "reduce": "sum(fp64 fold)/min/max", "launch": "one persistent "
+                       "launch per step, replayed from a CUDA graph",
+                       "l2": "no flush: inputs 1 GiB per step, 8x the L2",
+                       "parallelism": "dp%d (one rank per GPU, own partitions)" % world},
+            "fraction_of_hbm": value / world / pk,
+            "elements_per_s": world * PARTS * PART_N / (step_ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+                         "frac": achieved / pk, "traffic": committed_traffic(),
+                         "kernel": "k_persistent<F32>", "peak_source": peaks()["source"] +
+                         " (MEASURED_PEAKS.json hbm_gbs, copy)"},
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "launches_per_step": launches_per_step,
+            "clocks": clocks,
+            "check": check,
+            "cpu_baseline": cpu,
+        }
+        if configs is not None:
+            line["configs"] = configs
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="headline only")
+    ap.add_argument("--full", action="store_true", help="longer serving runs")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="profiler case: headline kernel only, small arena, no JSON line")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -447,7 +447,8 @@ int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks, scl_b
     if (st == SCL_OK && ntasks) {
         if (cudaMemcpy(b->img.block, host.data(), b->img.plan_bytes, cudaMemcpyHostToDevice) !=
                 cudaSuccess ||
-            cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes) != cudaSuccess)
+            cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)   // order before launches on any stream
             st = fail(SCL_E_CUDA, "uploading the batch plan failed");
     }
     if (st != SCL_OK) {

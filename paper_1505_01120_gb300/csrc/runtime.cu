@@ -207,7 +207,12 @@ static int grow(Ctx* c, void** p, size_t* cap, size_t need, size_t elem, bool ze
     }
     void* q = c->arena.alloc(pow2 * elem);
     if (!q) return fail(SCL_E_NOMEM, "arena: no block of %zu bytes for scratch", pow2 * elem);
-    if (zero) SCL_CUDA(cudaMemset(q, 0, pow2 * elem));
+    if (zero) {
+        // cudaMemset runs on the legacy stream, which does not order against
+        // non-blocking streams: finish it before any launch can see the block
+        SCL_CUDA(cudaMemset(q, 0, pow2 * elem));
+        SCL_CUDA(cudaDeviceSynchronize());
+    }
     blocks.push_back(q);
     *p = q;
     *cap = pow2;
@@ -220,6 +225,7 @@ int ensure_scratch(Ctx* c, Scratch* s, size_t tasks, size_t sslots, size_t kslot
         void* h = c->arena.alloc(H_WORDS * 4);
         if (!h) return fail(SCL_E_NOMEM, "arena: no room for scratch header");
         SCL_CUDA(cudaMemset(h, 0, H_WORDS * 4));
+        SCL_CUDA(cudaDeviceSynchronize());
         s->hdr = (uint32_t*)h;
         s->blocks.push_back(h);
     }
