@@ -35,6 +35,7 @@ SCL_U32, SCL_I32, SCL_F32, SCL_KV_I32_F32 = 0, 1, 2, 3
 SCL_K_IDENT, SCL_K_MIX32, SCL_K_POLY3 = 0, 1, 2
 # scl_reduce
 SCL_R_NONE, SCL_R_SUM, SCL_R_SUM_MIN_MAX, SCL_R_KEYED_COUNT_SUM = 0, 1, 2, 3
+SCL_NOALLOC_MAX_ELEMENTS = 67_108_864
 
 
 class scl_config(ctypes.Structure):
@@ -122,6 +123,8 @@ _SIGS = {
     "scl_batch_kernel_launches": ([_P, ctypes.POINTER(_u32)], ctypes.c_int),
     "scl_batch_destroy": ([_P], ctypes.c_int),
     "scl_batch_run": ([_P, _P, _u32, _P, _P], ctypes.c_int),
+    "scl_map_reduce_noalloc": ([_P, ctypes.c_int, _u64, ctypes.c_int, _P, ctypes.c_int, _P, _P],
+                               ctypes.c_int),
 }
 
 for _name, (_args, _res) in _SIGS.items():
@@ -358,3 +361,13 @@ def scl_batch_run(ctx: int, tasks: ctypes.Array, ntasks: int, stream: int = 0,
     _check(lib.scl_batch_run(ctx, ctypes.cast(tasks, ctypes.c_void_p), ntasks, stream,
                              out.ctypes.data), allow)
     return out[:ntasks]
+
+
+def scl_map_reduce_noalloc(dev_in, dtype: int, n: int, kernel: int, reduce: int, dev_out,
+                           coef=None, stream: int = 0) -> None:
+    """Map + reduce without any allocation (see include/scl.h): for callers
+    that cannot allocate device memory when they need the result.  Inputs and
+    the scl_result slot are device addresses the caller owns."""
+    c = _coef(coef)
+    _check(lib.scl_map_reduce_noalloc(_ptr(dev_in), dtype, n, kernel, _ptr(c), reduce, stream,
+                                      _ptr(dev_out)))
