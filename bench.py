@@ -312,6 +312,83 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
     del dk, dv, outs
 
     out["batch_10000"] = batch_config(torch, scl, ctx, stream)
+    out["serve"] = serve_config(torch, scl, ctx, stream, full)
+    return out
+
+
+def serve_config(torch, scl, ctx, stream, full: bool) -> dict:
+    """Open-loop Poisson arrivals over a pool of resident partitions whose sizes
+    follow the serving distribution (log-normal, median 2^18, sigma 1.5,
+    clipped [1,024, 67,108,864]); kernels uniform over the three.  Batched:
+    continuous batching, 4 launches in flight.  Unbatched: one launch per task,
+    one in flight, FIFO.  Latency = completion - scheduled arrival."""
+    import oracle
+    rng = np.random.default_rng(5)
+    pool = 240
+    sizes = synth.lognormal_sizes(pool, 1 << 18, 1.5, 1024, 1 << 26, rng)
+    kinds = np.arange(pool) % 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    bufs, tasks = [], []
+    for n, k in zip(sizes, kinds):
+        n = int(n)
+        if k == synth.KIND_MIX32:
+            b = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device="cuda",
+                              generator=g)
+            q = scl.scl_wrap_device(ctx.handle, b.data_ptr(), None, scl.SCL_U32, n)
+            tasks.append(dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_SUM))
+            bufs.append((b,))
+        elif k == synth.KIND_POLY3:
+            b = torch.randn(n, device="cuda", generator=g)
+            q = scl.scl_wrap_device(ctx.handle, b.data_ptr(), None, scl.SCL_F32, n)
+            tasks.append(dict(part=q, kernel=scl.SCL_K_POLY3, reduce=scl.SCL_R_SUM_MIN_MAX))
+            bufs.append((b,))
+        else:
+            kk = torch.randint(0, 4096, (n,), dtype=torch.int32, device="cuda", generator=g)
+            vv = torch.rand(n, device="cuda", generator=g)
+            o = torch.zeros(4096 * 2, dtype=torch.int32, device="cuda")
+            q = scl.scl_wrap_device(ctx.handle, kk.data_ptr(), vv.data_ptr(),
+                                    scl.SCL_KV_I32_F32, n)
+            tasks.append(dict(part=q, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                              num_keys=4096, counts_out=o.data_ptr(),
+                              sums_out=o.data_ptr() + 16384))
+            bufs.append((kk, vv, o))
+    torch.cuda.synchronize()
+    pool_bytes = int(sum(int(n) * (8 if k == synth.KIND_KEYED else 4)
+                         for n, k in zip(sizes, kinds)))
+    secs = 20.0 if full else 1.0
+    out = {"pool_partitions": pool, "pool_bytes": pool_bytes,
+           "size_median": 1 << 18, "size_sigma": 1.5, "duration_s": secs,
+           "hbm_budget_bytes": 120 * 10**9, "rates": {}}
+    for rate in (2000, 10000, 50000):
+        n = int(rate * secs)
+        arrivals = synth.poisson_arrivals(float(rate), n, np.random.default_rng(50 + rate))
+        pick = np.random.default_rng(60 + rate).integers(0, pool, size=n)
+        arr = scl.make_tasks([tasks[i] for i in pick])
+        mean_bytes = float(np.mean([int(sizes[i]) * (8 if kinds[i] == 2 else 4) for i in pick]))
+        row = {"tasks": n, "offered_gbs": rate * mean_bytes / 1e9}
+        for mode, k, mb in (("batched", 4, 4096), ("unbatched", 1, 1)):
+            scl.scl_server_start(ctx.handle, inflight_batches=k, max_batch_tasks=mb,
+                                 hbm_budget_bytes=120 * 10**9)
+            t0 = time.perf_counter()
+            lat, res = scl.scl_server_replay(ctx.handle, arr, arrivals, n)
+            wall = time.perf_counter() - t0 - 1e-3
+            st = scl.scl_server_get_stats(ctx.handle)
+            scl.scl_server_stop(ctx.handle)
+            ok = bool(np.all(res["status"] == 0))
+            row[mode] = {"tasks_per_s": n / wall, "p50_us": float(np.percentile(lat, 50)) / 1e3,
+                         "p99_us": float(np.percentile(lat, 99)) / 1e3,
+                         "p999_us": float(np.percentile(lat, 99.9)) / 1e3,
+                         "batches": int(st["batches"]), "max_batch": int(st["max_batch"]),
+                         "all_ok": ok}
+            if mode == "batched":
+                # spot check a served uint32 result against the oracle
+                j = next(j for j in range(n) if kinds[pick[j]] == synth.KIND_MIX32)
+                h = bufs[pick[j]][0].cpu().numpy().view(np.uint32)
+                row[mode]["spot_check_bit_exact"] = int(res[j]["u64_sum"]) == oracle.sum_u32(h)
+        out["rates"][str(rate)] = row
+    for t in tasks:
+        scl.scl_free_partition(ctx.handle, t["part"])
     return out
 
 

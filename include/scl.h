@@ -268,6 +268,63 @@ int scl_combine_keyed(const uint32_t* counts, const double* sums64, uint32_t k,
                       uint32_t num_keys, uint32_t* counts_out,
                       double* sums64_out);
 
+/* ------------------------------------------------------------ launch shapes */
+
+/* Kernel families, each with its own launch shape. */
+#define SCL_FAMILY_U32   0   /* uint32 partitions: mix32 / identity + uint64 sum     */
+#define SCL_FAMILY_F32   1   /* fp32 partitions: poly3 / identity + sum / min / max  */
+#define SCL_FAMILY_KEYED 2   /* keyed count + sum                                     */
+#define SCL_FAMILY_MIXED 3   /* batches mixing families (uses the F32 block and
+                                items per thread, its own CTAs per SM)                */
+
+/* Launch shape of one kernel family: what the autotuner chooses.  A chunk is
+ * block * items_per_thread * 4 elements; streaming partitions are cut into
+ * segments of 1..4 chunks, so (block, items_per_thread) also fixes how fp32
+ * sums are grouped -- results are bitwise stable for a fixed shape.  path 1
+ * (TMA bulk-copy pipeline, one extra producer warp) exists for the U32 and
+ * F32 families and gives bit-identical results to path 0 of the same
+ * (block, items_per_thread). */
+typedef struct {
+    int32_t block;             /* data threads per CTA: 256 or 512               */
+    int32_t items_per_thread;  /* 128-bit vectors per thread per chunk: 2, 4, 8  */
+    int32_t ctas_per_sm;       /* resident CTAs per SM; 0 = as many as fit       */
+    int32_t path;              /* 0 = vector loads, 1 = TMA bulk-copy pipeline   */
+    int32_t stages;            /* TMA ring depth; 0 = the shape's default        */
+    int32_t reserved;
+} scl_shape;
+
+/* Read / set a family's launch shape.  scl_set_shape returns
+ * SCL_E_UNSUPPORTED for a shape that is not compiled into the library.  A
+ * batch keeps the shape it was created with. */
+int scl_get_shape(scl_ctx* ctx, int family, scl_shape* out);
+int scl_set_shape(scl_ctx* ctx, int family, const scl_shape* shape);
+
+/* Autotuner configuration; every field may be 0 for its default. */
+typedef struct {
+    uint64_t probe_bytes;   /* bytes of the large probe partitions (256 MiB)     */
+    uint32_t reps;          /* timed launches per candidate (10)                 */
+    uint32_t families;      /* bit (1 << SCL_FAMILY_*) per family to tune (all)  */
+} scl_autotune_config;
+
+typedef struct {
+    scl_shape chosen[4];    /* per family, the shape now in effect               */
+    double best_ms[4];      /* its probe time (large + small batch), ms          */
+    uint32_t candidates[4]; /* candidates timed                                  */
+} scl_autotune_report;
+
+/* Choose each family's launch shape by measurement: block size, items per
+ * thread, CTAs per SM, load path and TMA ring depth.  Probe partitions
+ * (a few large, 512 of 16,384 elements) are filled on the device in the
+ * arena and every compiled candidate is timed with CUDA events on `stream`;
+ * the fastest (sum of both probe batches) is kept.  The FP32 family is tuned
+ * first; MIXED inherits its block and items per thread.  If the context has a
+ * tune cache path, the result is written there and loaded by later contexts
+ * on a GPU with the same SM count.  cfg and report may be NULL.  Takes about a
+ * second; the arena needs about 4 x probe_bytes free (the probe shrinks to
+ * fit, down to 16 MiB).  Errors: SCL_E_NOMEM, SCL_E_CUDA, SCL_E_TIMEOUT. */
+int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
+                 scl_autotune_report* report);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Plan many partition tasks as ONE persistent launch (thousands of uneven
@@ -335,6 +392,75 @@ int scl_batch_run(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
 int scl_map_reduce_noalloc(const void* dev_in, scl_dtype dtype, uint64_t n,
                            scl_map_kernel kernel, const float coef[3],
                            scl_reduce reduce, void* stream, scl_result* dev_out);
+
+/* ----------------------------------------------------------------- server */
+
+/* The continuous-batching server.  The paper serialises acceleration tasks
+ * per device by giving each accelerator worker one core (Sec. 3.1.5) and asks
+ * for enough data per offload (Sec. 3 items 1-2); here tasks that arrive
+ * while others run are admitted as HBM budget frees, packed into the next
+ * persistent launch, and overlap on the device with batches already running.
+ *
+ * Admission: a task is charged an estimate of its device working set (plan
+ * entry, segment partials, keyed tables, and its input if it brings new data);
+ * it enters the GPU queue when partitions resident in the arena + working sets
+ * of admitted tasks + its own fit hbm_budget_bytes, otherwise it waits FIFO.
+ * A task that can never fit is rejected with SCL_E_BUDGET. */
+typedef struct {
+    int32_t inflight_batches;   /* launches on the GPU at once, one stream each
+                                   (1..16; 0 = 4)                                  */
+    uint32_t max_batch_tasks;   /* tasks per launch (1..65536; 0 = 4096);
+                                   1 = unbatched: one launch per task             */
+    uint64_t hbm_budget_bytes;  /* 0 = scl_config's budget, else the arena size    */
+    uint64_t reserved[2];
+} scl_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    uint64_t batches, max_batch, kernel_launches;
+    uint64_t admission_waits;    /* tasks that waited for budget                   */
+    uint64_t budget_bytes, resident_bytes, bytes_in_use, peak_bytes_in_use;
+} scl_server_stats;
+
+/* Start the server threads (batcher + completion) on this context.  Only one
+ * server per context.  Partitions referenced by tasks must stay alive until
+ * their tasks complete.  Errors: SCL_E_STATE (already running). */
+int scl_server_start(scl_ctx* ctx, const scl_server_config* cfg);
+
+/* Submit one task on a resident partition; returns at once with a ticket.
+ * Keyed tasks write their tables to the task's device arrays.  Thread-safe.
+ * Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED, SCL_E_BUDGET, SCL_E_STATE. */
+int scl_server_submit(scl_ctx* ctx, const scl_task* task, uint64_t* ticket);
+
+/* Submit a task that brings new data (mapParameters' copy, Sec. 3.1.1.1):
+ * host0[n] (and host1[n] for keyed) are copied to a transient partition when
+ * the task is admitted, and freed when it completes; the copy counts in the
+ * task's latency.  The host arrays must stay valid until the task completes
+ * (pinned memory copies asynchronously).  task->part is ignored. */
+int scl_server_submit_load(scl_ctx* ctx, const void* host0, const void* host1,
+                           scl_dtype dtype, uint64_t n, const scl_task* task,
+                           uint64_t* ticket);
+
+/* SCL_OK and the result once the task is done (the ticket is then retired),
+ * SCL_E_PENDING before.  A failed task has its status in out->status. */
+int scl_server_poll(scl_ctx* ctx, uint64_t ticket, scl_result* out);
+
+/* Block until the task is done or timeout_ms passes (SCL_E_TIMEOUT). */
+int scl_server_wait(scl_ctx* ctx, uint64_t ticket, uint32_t timeout_ms,
+                    scl_result* out);
+
+int scl_server_get_stats(scl_ctx* ctx, scl_server_stats* out);
+
+/* Drain admitted work, stop the threads, release the server.  No-op if not
+ * running.  Called by scl_destroy. */
+int scl_server_stop(scl_ctx* ctx);
+
+/* Open-loop trace driver: submit tasks[i] at arrival_s[i] seconds after the
+ * start (scheduled, not when the previous task finished), then wait for all.
+ * latency_ns[i] = completion time - scheduled arrival (may be NULL);
+ * results[i] the result (may be NULL).  Runs on the calling thread. */
+int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s,
+                      uint32_t n, int64_t* latency_ns, scl_result* results);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,8 @@ int scl_create(const scl_config* cfg, scl_ctx** out) {
     scl_ctx* c = new (std::nothrow) scl_ctx();
     if (!c) return fail(SCL_E_NOMEM, "host allocation failed");
     c->device = cfg->device;
+    c->arena_bytes = cfg->arena_bytes;
+    c->hbm_budget = cfg->hbm_budget_bytes;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device);
     c->arena.init((char*)cfg->arena, cfg->arena_bytes);
@@ -108,7 +110,7 @@ int scl_create(const scl_config* cfg, scl_ctx** out) {
     c->d_kout = (uint32_t*)c->arena.alloc((size_t)kMaxKeys * 16);
     int st = SCL_OK;
     if (!c->d_result || !c->d_kout) st = fail(SCL_E_NOMEM, "arena too small");
-    if (st == SCL_OK && cudaHostAlloc((void**)&c->h_result, sizeof(scl_result),
+    if (st == SCL_OK && cudaHostAlloc((void**)&c->h_result, 2 * sizeof(scl_result),
                                       cudaHostAllocDefault) != cudaSuccess)
         st = fail(SCL_E_CUDA, "cudaHostAlloc failed");
     if (st == SCL_OK) st = ensure_scratch(c, &c->single, 1, 0, 0, kMaxKeys / kFoldBlock);
@@ -164,6 +166,7 @@ static int new_partition(scl_ctx* c, scl_dtype dt, uint64_t n, Partition* p) {
 static scl_part register_partition(scl_ctx* c, const Partition& p) {
     const scl_part h = c->next_part++;
     c->parts[h] = p;
+    if (p.block) c->resident_bytes += align_up(p.n * 4) * dtype_words(p.dtype);
     return h;
 }
 
@@ -232,6 +235,7 @@ int scl_free_partition(scl_ctx* ctx, scl_part part) {
         // stream-ordered work may still read it
         SCL_CUDA(cudaDeviceSynchronize());
         ctx->arena.release(it->second.block);
+        ctx->resident_bytes -= align_up(it->second.n * 4) * dtype_words(it->second.dtype);
     }
     ctx->parts.erase(it);
     return SCL_OK;
@@ -318,14 +322,34 @@ static int map_reduce_common(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
     return run_single(ctx, *p, kind, coef, 0, nullptr, nullptr, nullptr, dev_out, S(stream));
 }
 
+// After a synchronous single call: a non-zero device error word means a
+// bounded wait expired (or an unknown work kind was met); report it and reset
+// the single-call scratch so the next launch starts clean.
+static int check_single_error(scl_ctx* ctx) {
+    const uint32_t err = *reinterpret_cast<uint32_t*>(ctx->h_result + 1);
+    if (!err) return SCL_OK;
+    SCL_CUDA(cudaMemset(ctx->single.hdr, 0, H_WORDS * 4));
+    SCL_CUDA(cudaMemset(ctx->single.tickets, 0, ctx->single.task_cap * 4));
+    SCL_CUDA(cudaDeviceSynchronize());
+    return fail((err & 4u) ? SCL_E_TIMEOUT : SCL_E_STATE,
+                "device error word 0x%x after the launch", err);
+}
+
+static int fetch_single(scl_ctx* ctx, cudaStream_t st) {
+    SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
+                             cudaMemcpyDeviceToHost, st));
+    SCL_CUDA(cudaMemcpyAsync(ctx->h_result + 1, ctx->single.hdr + H_ERROR, 4,
+                             cudaMemcpyDeviceToHost, st));
+    SCL_CUDA(cudaStreamSynchronize(st));
+    return check_single_error(ctx);
+}
+
 int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const float coef[3],
                    scl_reduce reduce, void* stream, scl_result* out) {
     CTX_ENTER(ctx);
     if (!out) return fail(SCL_E_INVALID, "null output");
     SCL_TRY(map_reduce_common(ctx, part, kernel, coef, reduce, stream, ctx->d_result));
-    SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
-                             cudaMemcpyDeviceToHost, S(stream)));
-    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    SCL_TRY(fetch_single(ctx, S(stream)));
     *out = *ctx->h_result;
     return SCL_OK;
 }
@@ -360,9 +384,7 @@ int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* strea
     SCL_CUDA(cudaMemcpyAsync(sums_out, ds, num_keys * 4, cudaMemcpyDeviceToHost, S(stream)));
     if (sums64_out)
         SCL_CUDA(cudaMemcpyAsync(sums64_out, d64, num_keys * 8, cudaMemcpyDeviceToHost, S(stream)));
-    SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
-                             cudaMemcpyDeviceToHost, S(stream)));
-    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    SCL_TRY(fetch_single(ctx, S(stream)));
     if (result) *result = *ctx->h_result;
     if (ctx->h_result->status == SCL_E_KEY_RANGE)
         return fail(SCL_E_KEY_RANGE, "a key outside [0, %u) was skipped", num_keys);
@@ -429,6 +451,44 @@ int scl_combine_keyed(const uint32_t* counts, const double* sums64, uint32_t k, 
         }
     }
     return SCL_OK;
+}
+
+// ------------------------------------------------------------ launch shapes
+
+int scl_get_shape(scl_ctx* ctx, int family, scl_shape* out) {
+    CTX_ENTER(ctx);
+    if (!out || family < 0 || family >= M_NUM) return fail(SCL_E_INVALID, "bad family or output");
+    const Shape s = ctx->shape_for(family);
+    out->block = s.block;
+    out->items_per_thread = s.ipt;
+    out->ctas_per_sm = s.ctas_per_sm;
+    out->path = s.path;
+    out->stages = find_entry(family, s) ? find_entry(family, s)->stages : s.stages;
+    out->reserved = 0;
+    return SCL_OK;
+}
+
+int scl_set_shape(scl_ctx* ctx, int family, const scl_shape* in) {
+    CTX_ENTER(ctx);
+    if (!in || family < 0 || family >= M_NUM) return fail(SCL_E_INVALID, "bad family or shape");
+    Shape s{in->block, in->items_per_thread, in->ctas_per_sm, in->path, in->stages};
+    if (in->ctas_per_sm < 0) return fail(SCL_E_INVALID, "ctas_per_sm must be >= 0");
+    if (family == M_ALL) {   // block / items per thread follow the F32 family
+        s.block = ctx->shape[M_F32].block;
+        s.ipt = ctx->shape[M_F32].ipt;
+        if (in->path != PATH_LDG) return fail(SCL_E_UNSUPPORTED, "mixed batches use path 0");
+    }
+    if (!find_entry(family, s))
+        return fail(SCL_E_UNSUPPORTED, "shape %d x %d path %d stages %d is not compiled",
+                    s.block, s.ipt, s.path, s.stages);
+    ctx->shape[family] = s;
+    return SCL_OK;
+}
+
+int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
+                 scl_autotune_report* report) {
+    CTX_ENTER(ctx);
+    return autotune(ctx, cfg, S(stream), report);
 }
 
 // ----------------------------------------------------------------- batches
@@ -502,10 +562,20 @@ int scl_batch_results(scl_batch* b, void* stream, scl_result* results) {
     if (!b) return fail(SCL_E_INVALID, "null batch");
     CTX_ENTER(b->ctx);
     if (b->ntasks && !results) return fail(SCL_E_INVALID, "null results");
-    if (b->ntasks)
+    uint32_t err = 0;
+    if (b->ntasks) {
         SCL_CUDA(cudaMemcpyAsync(results, b->img.results, b->ntasks * sizeof(scl_result),
                                  cudaMemcpyDeviceToHost, S(stream)));
+        SCL_CUDA(cudaMemcpyAsync(&err, b->img.hdr + H_ERROR, 4, cudaMemcpyDeviceToHost,
+                                 S(stream)));
+    }
     SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    if (err) {
+        SCL_CUDA(cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes));
+        SCL_CUDA(cudaDeviceSynchronize());
+        return fail((err & 4u) ? SCL_E_TIMEOUT : SCL_E_STATE,
+                    "device error word 0x%x after the batch", err);
+    }
     for (uint32_t i = 0; i < b->ntasks; ++i)
         if (results[i].status == SCL_E_KEY_RANGE)
             return fail(SCL_E_KEY_RANGE, "task %u saw a key out of range", i);

@@ -138,13 +138,19 @@ __host__ __device__ inline uint32_t keyed_single_pieces(uint64_t n, uint32_t gri
 
 // Host-side launch entry of one compiled persistent-kernel instantiation.
 struct KernelEntry {
-    int mask, block, ipt;
+    int mask, block, ipt;              // block = threads that touch data (consumers)
     const void* fn;                    // __global__ function pointer
     size_t dyn_smem;                   // dynamic shared memory per CTA
+    int path;                          // PATH_LDG or PATH_TMA
+    int stages;                        // TMA ring stages (0 for LDG)
 };
 
+enum Path : int { PATH_LDG = 0, PATH_TMA = 1 };
+
+// Threads launched per CTA: TMA kernels add one producer warp.
+inline int launch_threads(const KernelEntry& e) { return e.block + (e.path == PATH_TMA ? 32 : 0); }
+
 // Provided by the kernel translation units.
-extern const KernelEntry* kernel_table(int mask, int* count);
 extern const void* fold_kernel_fn();
 extern const void* map_kernel_fn(int kind, int aligned);
 extern int map_kernel_block();

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(BLOCK) k_map(const void* in, void* out, uint64
 // Instantiate the persistent kernel for one mask over the tuned shapes and
 // define kernel_table_<name>().
 #define SCL_DYN(M) (scl::mask_has_keyed(M) ? scl::kKeyedSmemBytes : 0)
-#define SCL_SHAPE(M, B, I) {M, B, I, (const void*)&scl::dev::k_persistent<B, I, M>, SCL_DYN(M)}
+#define SCL_SHAPE(M, B, I) {M, B, I, (const void*)&scl::dev::k_persistent<B, I, M>, SCL_DYN(M), 0, 0}
 #define SCL_DEFINE_TABLE(NAME, M)                                                   \
     namespace scl {                                                                 \
     const KernelEntry* kernel_table_##NAME(int* count) {                            \

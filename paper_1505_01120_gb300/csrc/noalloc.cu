@@ -11,9 +11,9 @@
 // below, which every GPU that loads the library keeps until the process exits.
 //
 // The kernel is the same persistent map/reduce kernel the context API uses,
-// at the default launch shape (256 threads, 4 vectors per thread), so a
-// result equals what scl_map_reduce returns for the same partition when that
-// context runs at the default shape.
+// at the launch shape 256 threads x 4 vectors per thread, so a result equals
+// what scl_map_reduce returns for the same partition when that context's
+// family runs at that shape (scl_set_shape).
 #include <stddef.h>
 #include <string.h>
 

@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <atomic>
 #include <fstream>
+#include <map>
+#include <mutex>
 #include <sstream>
 
 #include "runtime.h"
@@ -17,6 +19,8 @@ const KernelEntry* kernel_table_u32(int* count);
 const KernelEntry* kernel_table_f32(int* count);
 const KernelEntry* kernel_table_keyed(int* count);
 const KernelEntry* kernel_table_all(int* count);
+const KernelEntry* kernel_table_tma_u32(int* count);
+const KernelEntry* kernel_table_tma_f32(int* count);
 
 // ------------------------------------------------------------------ errors
 
@@ -113,12 +117,35 @@ static const KernelEntry* table(int mask, int* count) {
     }
 }
 
-const KernelEntry* find_entry(int mask, int block, int ipt) {
+const KernelEntry* find_entry(int mask, int block, int ipt, int path, int stages) {
     int n = 0;
-    const KernelEntry* t = table(mask, &n);
+    const KernelEntry* t = nullptr;
+    if (path == PATH_TMA) {
+        if (mask == M_U32) t = kernel_table_tma_u32(&n);
+        else if (mask == M_F32) t = kernel_table_tma_f32(&n);
+        else return nullptr;
+    } else {
+        t = table(mask, &n);
+    }
     for (int i = 0; i < n; ++i)
-        if (t[i].block == block && t[i].ipt == ipt) return &t[i];
+        if (t[i].block == block && t[i].ipt == ipt && (stages == 0 || t[i].stages == stages))
+            return &t[i];
     return nullptr;
+}
+
+int prepare_entry(const KernelEntry* e) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, bool> done;
+    int dev = 0;
+    SCL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(e->fn, dev);
+    if (done.count(key)) return SCL_OK;
+    if (e->dyn_smem > 48 * 1024)
+        SCL_CUDA(cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)e->dyn_smem));
+    done[key] = true;
+    return SCL_OK;
 }
 
 int mask_of_kind(uint32_t kind) {
@@ -166,24 +193,26 @@ Shape Ctx::shape_for(int mask) const {
     if (mask == M_ALL) {
         s.block = shape[M_F32].block;
         s.ipt = shape[M_F32].ipt;
+        s.path = PATH_LDG;
+        s.stages = 0;
     }
     return s;
 }
 
 uint32_t Ctx::grid_max(int mask, const Shape& sh) {
-    const KernelEntry* e = find_entry(mask, sh.block, sh.ipt);
+    const KernelEntry* e = find_entry(mask, sh);
     if (!e) return 1;
-    auto key = std::make_pair(e->fn, 0);
     int nb = 0;
-    auto it = occ_cache.find(key);
+    auto it = occ_cache.find(e->fn);
     if (it != occ_cache.end()) {
         nb = it->second;
     } else {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e->fn, sh.block, e->dyn_smem) !=
-            cudaSuccess)
+        if (prepare_entry(e) != SCL_OK ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e->fn, launch_threads(*e),
+                                                          e->dyn_smem) != cudaSuccess)
             nb = 1;
         if (nb < 1) nb = 1;
-        occ_cache[key] = nb;
+        occ_cache[e->fn] = nb;
     }
     const int per = sh.ctas_per_sm > 0 ? std::min(sh.ctas_per_sm, nb) : nb;
     return (uint32_t)(sms * per);
@@ -276,10 +305,11 @@ void fill_task(DevTask* t, const Partition& p, uint32_t kind, const float* coef,
 
 // --------------------------------------------------------- single launches
 
-static int launch_kernel(const void* fn, uint32_t grid, uint32_t block, size_t smem,
-                         const KernelArgs& args, cudaStream_t st) {
+static int launch_entry(const KernelEntry* e, uint32_t grid, const KernelArgs& args,
+                        cudaStream_t st) {
+    SCL_TRY(prepare_entry(e));
     void* params[] = {const_cast<KernelArgs*>(&args)};
-    SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, st));
+    SCL_CUDA(cudaLaunchKernel(e->fn, dim3(grid), dim3(launch_threads(*e)), params, e->dyn_smem, st));
     count_launches(1);
     return SCL_OK;
 }
@@ -289,7 +319,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
                cudaStream_t st) {
     const int mask = mask_of_kind(kind);
     const Shape sh = c->shape_for(mask);
-    const KernelEntry* e = find_entry(mask, sh.block, sh.ipt);
+    const KernelEntry* e = find_entry(mask, sh);
     if (!e) return fail(SCL_E_STATE, "no kernel for shape %d x %d", sh.block, sh.ipt);
     const uint32_t gmax = c->grid_max(mask, sh);
 
@@ -322,7 +352,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     a.tickets = c->single.tickets;
     a.task_flags = c->single.flags;
     a.hdr = c->single.hdr;
-    SCL_TRY(launch_kernel(e->fn, grid, sh.block, e->dyn_smem, a, st));
+    SCL_TRY(launch_entry(e, grid, a, st));
     if (kind == K_KEYED && t.nseg > 1) {
         const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;
         void* params[] = {&a};
@@ -363,7 +393,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     const int ntypes = (int)has_u32 + (int)has_f32 + (int)has_keyed;
     P->mask = ntypes > 1 ? M_ALL : has_keyed ? M_KEYED : has_f32 ? M_F32 : M_U32;
     P->shape = c->shape_for(P->mask);
-    if (!find_entry(P->mask, P->shape.block, P->shape.ipt))
+    if (!find_entry(P->mask, P->shape))
         return fail(SCL_E_STATE, "no kernel for shape %d x %d", P->shape.block, P->shape.ipt);
     const uint32_t gmax = c->grid_max(P->mask, P->shape);
     const uint32_t chunk = (uint32_t)(P->shape.block * P->shape.ipt * 4);
@@ -528,9 +558,9 @@ int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, Kernel
 int launch_plan(Ctx* c, const Plan& p, const KernelArgs& args, cudaStream_t st) {
     (void)c;
     if (p.tasks.empty()) return SCL_OK;
-    const KernelEntry* e = find_entry(p.mask, p.shape.block, p.shape.ipt);
+    const KernelEntry* e = find_entry(p.mask, p.shape);
     if (!e) return fail(SCL_E_STATE, "no kernel for the plan's shape");
-    SCL_TRY(launch_kernel(e->fn, p.grid, p.shape.block, e->dyn_smem, args, st));
+    SCL_TRY(launch_entry(e, p.grid, args, st));
     if (!p.fold_tasks.empty()) {
         void* params[] = {const_cast<KernelArgs*>(&args)};
         SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(p.fold_gridx, (uint32_t)p.fold_tasks.size()),
@@ -551,11 +581,12 @@ int load_tuning(Ctx* c, const char* path) {
     while (std::getline(f, line)) {
         std::istringstream is(line);
         std::string name;
-        int sms = 0, b = 0, ipt = 0, cps = 0;
-        if (!(is >> name >> sms >> b >> ipt >> cps)) continue;
+        int sms = 0, b = 0, ipt = 0, cps = 0, path = 0, stages = 0;
+        if (!(is >> name >> sms >> b >> ipt >> cps >> path >> stages)) continue;
         if (sms != c->sms) continue;
         for (int m = 0; m < M_NUM; ++m)
-            if (name == kMaskNames[m] && find_entry(m, b, ipt)) c->shape[m] = Shape{b, ipt, cps};
+            if (name == kMaskNames[m] && find_entry(m, b, ipt, path, stages))
+                c->shape[m] = Shape{b, ipt, cps, path, stages};
     }
     return SCL_OK;
 }
@@ -563,10 +594,11 @@ int load_tuning(Ctx* c, const char* path) {
 int save_tuning(Ctx* c, const char* path) {
     std::ofstream f(path);
     if (!f) return fail(SCL_E_INVALID, "cannot write tune cache %s", path);
-    f << "# mask sms block items_per_thread ctas_per_sm\n";
+    f << "# mask sms block items_per_thread ctas_per_sm path stages\n";
     for (int m = 0; m < M_NUM; ++m)
         f << kMaskNames[m] << " " << c->sms << " " << c->shape[m].block << " " << c->shape[m].ipt
-          << " " << c->shape[m].ctas_per_sm << "\n";
+          << " " << c->shape[m].ctas_per_sm << " " << c->shape[m].path << " "
+          << c->shape[m].stages << "\n";
     return SCL_OK;
 }
 

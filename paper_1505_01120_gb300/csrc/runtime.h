@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <condition_variable>
 #include <map>
 #include <memory>
@@ -76,12 +77,19 @@ struct Partition {
 // -------------------------------------------------------------- launch shape
 
 struct Shape {
-    int block = 256;
-    int ipt = 4;
+    int block = 256;       // threads that process data
+    int ipt = 4;           // 128-bit vectors per thread per chunk
     int ctas_per_sm = 0;   // 0 = as many as fit
+    int path = PATH_LDG;   // PATH_LDG or PATH_TMA (uint32 / fp32 kernels only)
+    int stages = 0;        // TMA ring depth (0 = first compiled for the shape)
 };
 
-const KernelEntry* find_entry(int mask, int block, int ipt);
+const KernelEntry* find_entry(int mask, int block, int ipt, int path = PATH_LDG, int stages = 0);
+inline const KernelEntry* find_entry(int mask, const Shape& s) {
+    return find_entry(mask, s.block, s.ipt, s.path, s.stages);
+}
+// Make a kernel launchable with its dynamic shared memory (idempotent).
+int prepare_entry(const KernelEntry* e);
 int mask_of_kind(uint32_t kind);
 int resolve_kind(scl_dtype dt, int kernel, int reduce, uint32_t* kind);
 
@@ -160,12 +168,18 @@ struct Ctx {
     int device = 0;
     int sms = 0;
     int l2_bytes = 0;
+    uint64_t arena_bytes = 0;
+    uint64_t hbm_budget = 0;                  // scl_config.hbm_budget_bytes
+    std::atomic<uint64_t> resident_bytes{0};  // bytes of partitions the library owns
     Arena arena;
     std::recursive_mutex mu;
     std::unordered_map<uint64_t, Partition> parts;
     uint64_t next_part = 1;
-    Shape shape[M_NUM];
-    std::map<std::pair<const void*, int>, int> occ_cache;
+    // Defaults: the fastest shapes measured on GB300 (vector-load kernels;
+    // the keyed kernel is bound by shared-memory atomics, not the shape).
+    Shape shape[M_NUM] = {Shape{256, 8, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0},
+                          Shape{256, 4, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0}};
+    std::map<const void*, int> occ_cache;
     Scratch single;
     scl_result* d_result = nullptr;        // single-call result slot
     scl_result* h_result = nullptr;        // pinned
@@ -191,7 +205,8 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
 // Global count of kernel launches made by the library (graph replays included).
 void count_launches(uint64_t n);
 
-// Tuning cache.
+// Tuning cache and the autotuner.
+int autotune(Ctx* c, const scl_autotune_config* cfg, cudaStream_t st, scl_autotune_report* rep);
 int load_tuning(Ctx* c, const char* path);
 int save_tuning(Ctx* c, const char* path);
 

@@ -56,6 +56,37 @@ class scl_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
+class scl_shape(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("items_per_thread", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+SCL_FAMILY_U32, SCL_FAMILY_F32, SCL_FAMILY_KEYED, SCL_FAMILY_MIXED = 0, 1, 2, 3
+
+
+class scl_autotune_config(ctypes.Structure):
+    _fields_ = [("probe_bytes", ctypes.c_uint64), ("reps", ctypes.c_uint32),
+                ("families", ctypes.c_uint32)]
+
+
+class scl_autotune_report(ctypes.Structure):
+    _fields_ = [("chosen", scl_shape * 4), ("best_ms", ctypes.c_double * 4),
+                ("candidates", ctypes.c_uint32 * 4)]
+
+
+class scl_server_config(ctypes.Structure):
+    _fields_ = [("inflight_batches", ctypes.c_int32), ("max_batch_tasks", ctypes.c_uint32),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
+
+
+class scl_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "completed", "rejected", "batches", "max_batch", "kernel_launches",
+        "admission_waits", "budget_bytes", "resident_bytes", "bytes_in_use",
+        "peak_bytes_in_use")]
+
+
 class scl_task(ctypes.Structure):
     _fields_ = [("part", ctypes.c_uint64), ("kernel", ctypes.c_int32),
                 ("reduce", ctypes.c_int32), ("num_keys", ctypes.c_uint32),
@@ -123,6 +154,19 @@ _SIGS = {
     "scl_batch_kernel_launches": ([_P, ctypes.POINTER(_u32)], ctypes.c_int),
     "scl_batch_destroy": ([_P], ctypes.c_int),
     "scl_batch_run": ([_P, _P, _u32, _P, _P], ctypes.c_int),
+    "scl_get_shape": ([_P, ctypes.c_int, ctypes.POINTER(scl_shape)], ctypes.c_int),
+    "scl_set_shape": ([_P, ctypes.c_int, ctypes.POINTER(scl_shape)], ctypes.c_int),
+    "scl_autotune": ([_P, ctypes.POINTER(scl_autotune_config), _P,
+                      ctypes.POINTER(scl_autotune_report)], ctypes.c_int),
+    "scl_server_start": ([_P, ctypes.POINTER(scl_server_config)], ctypes.c_int),
+    "scl_server_submit": ([_P, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_server_submit_load": ([_P, _P, _P, ctypes.c_int, _u64, _P, ctypes.POINTER(_u64)],
+                               ctypes.c_int),
+    "scl_server_poll": ([_P, _u64, ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_server_wait": ([_P, _u64, _u32, ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_server_get_stats": ([_P, ctypes.POINTER(scl_server_stats)], ctypes.c_int),
+    "scl_server_stop": ([_P], ctypes.c_int),
+    "scl_server_replay": ([_P, _P, _P, _u32, _P, _P], ctypes.c_int),
     "scl_map_reduce_noalloc": ([_P, ctypes.c_int, _u64, ctypes.c_int, _P, ctypes.c_int, _P, _P],
                                ctypes.c_int),
 }
@@ -302,6 +346,95 @@ def scl_combine_keyed(counts: np.ndarray, sums64: np.ndarray | None):
         so = np.empty(nk, np.float64)
     _check(lib.scl_combine_keyed(_ptr(counts), _ptr(sums64), k, nk, _ptr(co), _ptr(so)))
     return co, so
+
+
+def scl_get_shape(ctx: int, family: int) -> dict:
+    s = scl_shape()
+    _check(lib.scl_get_shape(ctx, family, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_ if k != "reserved"}
+
+
+def scl_set_shape(ctx: int, family: int, block: int, items_per_thread: int,
+                  ctas_per_sm: int = 0, path: int = 0, stages: int = 0) -> None:
+    s = scl_shape(block=block, items_per_thread=items_per_thread, ctas_per_sm=ctas_per_sm,
+                  path=path, stages=stages)
+    _check(lib.scl_set_shape(ctx, family, ctypes.byref(s)))
+
+
+def scl_autotune(ctx: int, stream: int = 0, probe_bytes: int = 0, reps: int = 0,
+                 families: int = 0) -> list[dict]:
+    """Run the autotuner; returns per family the chosen shape, its probe time
+    and how many candidates were timed."""
+    cfg = scl_autotune_config(probe_bytes=probe_bytes, reps=reps, families=families)
+    rep = scl_autotune_report()
+    _check(lib.scl_autotune(ctx, ctypes.byref(cfg), stream, ctypes.byref(rep)))
+    out = []
+    for f in range(4):
+        s = rep.chosen[f]
+        out.append({"block": s.block, "items_per_thread": s.items_per_thread,
+                    "ctas_per_sm": s.ctas_per_sm, "path": s.path, "stages": s.stages,
+                    "best_ms": rep.best_ms[f], "candidates": rep.candidates[f]})
+    return out
+
+
+def scl_server_start(ctx: int, inflight_batches: int = 4, max_batch_tasks: int = 4096,
+                     hbm_budget_bytes: int = 0) -> None:
+    cfg = scl_server_config(inflight_batches=inflight_batches, max_batch_tasks=max_batch_tasks,
+                            hbm_budget_bytes=hbm_budget_bytes)
+    _check(lib.scl_server_start(ctx, ctypes.byref(cfg)))
+
+
+def scl_server_submit(ctx: int, tasks: ctypes.Array, index: int = 0) -> int:
+    t = _u64()
+    _check(lib.scl_server_submit(ctx, ctypes.byref(tasks[index]), ctypes.byref(t)))
+    return t.value
+
+
+def scl_server_submit_load(ctx: int, host0, host1, dtype: int, n: int, tasks: ctypes.Array,
+                           index: int = 0) -> int:
+    t = _u64()
+    _check(lib.scl_server_submit_load(ctx, _ptr(host0), _ptr(host1), dtype, n,
+                                      ctypes.byref(tasks[index]), ctypes.byref(t)))
+    return t.value
+
+
+def scl_server_poll(ctx: int, ticket: int):
+    """scl_result when done, None while pending."""
+    r = scl_result()
+    st = lib.scl_server_poll(ctx, ticket, ctypes.byref(r))
+    if st == SCL_E_PENDING:
+        return None
+    _check(st)
+    return r
+
+
+def scl_server_wait(ctx: int, ticket: int, timeout_ms: int = 60_000) -> scl_result:
+    r = scl_result()
+    _check(lib.scl_server_wait(ctx, ticket, timeout_ms, ctypes.byref(r)))
+    return r
+
+
+def scl_server_get_stats(ctx: int) -> dict:
+    s = scl_server_stats()
+    _check(lib.scl_server_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def scl_server_stop(ctx: int) -> None:
+    _check(lib.scl_server_stop(ctx))
+
+
+def scl_server_replay(ctx: int, tasks: ctypes.Array, arrival_s: np.ndarray, n: int,
+                      allow_errors: bool = False):
+    """Returns (latency_ns int64[n], results RESULT_DTYPE[n])."""
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.zeros(max(1, n), dtype=np.int64)
+    res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
+    st = lib.scl_server_replay(ctx, ctypes.cast(tasks, ctypes.c_void_p), arr.ctypes.data, n,
+                               lat.ctypes.data, res.ctypes.data)
+    if not allow_errors:
+        _check(st)
+    return lat[:n], res[:n]
 
 
 def make_tasks(specs) -> ctypes.Array:
