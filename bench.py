@@ -116,7 +116,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def window(self, t0: float, t1: float):
+        """Keep only samples taken between t0 and t1 (perf_counter)."""
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *exc):
         if self.proc:
@@ -129,7 +133,10 @@ class ClockSampler:
     def summary(self) -> dict:
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t0", -1e30), getattr(self, "t1", 1e30)
+        for ts, ln in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -529,11 +536,22 @@ def run_ours(args, rank: int, world: int):
             scl.scl_batch_launch(b, st)
             timer.stop()
         torch.cuda.synchronize()
-        elapsed = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        elapsed = t1 - t0
+        clk.window(t0, t1)
         if dist:
             dist.barrier()
     launches = scl.scl_kernel_launches_total() - before
     kernel_ms = timer.mean_ms()
+    combined = None
+    if dist:
+        # ReduceCL across ranks: fold every rank's 64 partition results on the
+        # host (a gloo side group; nothing on the data path), outside timing
+        from paper_1505_01120_gb300 import dist as sdist
+        gloo = dist.new_group(backend="gloo")
+        r = sdist.combine_across_ranks(res, group=gloo)
+        combined = {"partitions": world * PARTS, "n": int(r.n), "f64_sum": r.f64_sum,
+                    "f32_min": float(r.f32_min), "f32_max": float(r.f32_max)}
     step_ms = elapsed / args.steps * 1e3
     if dist:
         t = torch.tensor([step_ms], device="cuda")
@@ -548,21 +566,17 @@ def run_ours(args, rank: int, world: int):
         ctx.close()
         return
 
-    # end to end through the C ABI from pinned host buffers
-    scl.scl_batch_destroy(b)
-    for p in parts:
-        scl.scl_free_partition(ctx.handle, p)
-    e2e_steps = max(2, min(args.steps, 8))
+    # end to end through the C ABI from pinned host buffers: every step copies
+    # the 64 partitions' data from pinned host memory into the resident
+    # partitions, replays the batch and reads the 64 results back
+    e2e_steps = max(4, min(args.steps, 40))
+    hres = np.zeros(PARTS, dtype=scl.RESULT_DTYPE)
 
     def e2e_step():
-        ps = [scl.scl_load_partition(ctx.handle, hostv[i], scl.SCL_F32, stream=st)
-              for i in range(PARTS)]
-        tk = scl.make_tasks([dict(part=p, kernel=scl.SCL_K_POLY3,
-                                  reduce=scl.SCL_R_SUM_MIN_MAX) for p in ps])
-        r = scl.scl_batch_run(ctx.handle, tk, PARTS, stream=st)
-        for p in ps:
-            scl.scl_free_partition(ctx.handle, p)
-        return r
+        for i in range(PARTS):
+            scl.scl_reload_partition(ctx.handle, parts[i], hostv[i], None, stream=st)
+        scl.scl_batch_launch(b, st)
+        hres[:] = scl.scl_batch_results(b, PARTS, stream=st)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -572,13 +586,42 @@ def run_ours(args, rank: int, world: int):
     for _ in range(e2e_steps):
         e2e_step()
     e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    e2e_ok = bool(np.array_equal(hres["f64_sum"], res["f64_sum"]))
+
+    # the same through zero-copy partitions: kernels read the pinned host
+    # arrays directly over the host link, no staging copy
+    zparts = [scl.scl_wrap_device(ctx.handle, host.data_ptr() + i * PART_N * 4, None,
+                                  scl.SCL_F32, PART_N) for i in range(PARTS)]
+    zb = scl.scl_batch_create(ctx.handle, scl.make_tasks(
+        [dict(part=p, kernel=scl.SCL_K_POLY3, reduce=scl.SCL_R_SUM_MIN_MAX) for p in zparts]),
+        PARTS)
+    scl.scl_batch_launch(zb, st)
+    scl.scl_batch_results(zb, PARTS, stream=st)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        scl.scl_batch_launch(zb, st)
+        zres = scl.scl_batch_results(zb, PARTS, stream=st)
+    zc_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    zc_ok = bool(np.array_equal(zres["f64_sum"], res["f64_sum"]))
+    scl.scl_batch_destroy(zb)
+    for p in zparts:
+        scl.scl_free_partition(ctx.handle, p)
+    scl.scl_batch_destroy(b)
+    for p in parts:
+        scl.scl_free_partition(ctx.handle, p)
     if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
+        t = torch.tensor([e2e_ms, zc_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, zc_ms = float(t[0].item()), float(t[1].item())
     e2e = {"value": world * STEP_BYTES / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": STEP_BYTES, "d2h_bytes_per_step": PARTS * 48,
-           "ms_per_step": e2e_ms}
+           "ms_per_step": e2e_ms, "results_equal_device_resident": e2e_ok,
+           "path": "scl_reload_partition x64 (pinned H2D) + batch graph replay + "
+                   "scl_batch_results"}
+    e2e_zero_copy = {"value": world * STEP_BYTES / (zc_ms * 1e-3) / 1e9, "unit": "GB/s",
+                     "h2d_bytes_per_step": STEP_BYTES, "d2h_bytes_per_step": PARTS * 48,
+                     "ms_per_step": zc_ms, "results_equal_device_resident": zc_ok,
+                     "path": "partitions wrapped on pinned host memory, read by the kernel"}
 
     configs, cpu = None, None
     if rank == 0 and world == 1:
@@ -610,10 +653,12 @@ def run_ours(args, rank: int, world: int):
                          "kernel": "k_persistent<F32>", "peak_source": peaks()["source"] +
                          " (MEASURED_PEAKS.json hbm_gbs, copy)"},
             "e2e": e2e,
+            "e2e_zero_copy": e2e_zero_copy,
             "gpu_launches": int(launches),
             "launches_per_step": launches_per_step,
             "clocks": clocks,
             "check": check,
+            "combined_across_ranks": combined,
             "cpu_baseline": cpu,
         }
         if configs is not None:
@@ -627,7 +672,7 @@ def run_ours(args, rank: int, world: int):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="headline only")

@@ -189,10 +189,22 @@ int scl_load_partition_kv(scl_ctx* ctx, const int32_t* keys, const float* vals,
 
 /* Wrap caller-owned device arrays as a partition without copying (e.g. a
  * torch tensor's data_ptr).  dev1 is the value array for SCL_KV_I32_F32 and
- * must be NULL otherwise.  The arrays must outlive the handle.  Any
- * alignment is accepted (16-byte aligned arrays take the vector path). */
+ * must be NULL otherwise.  The arrays must outlive the handle.  4-byte
+ * alignment is required (16-byte aligned arrays take the vector path).  Any
+ * address the GPU can load from works, including pinned host memory: kernels
+ * then stream the partition straight from host memory over the host link
+ * (no staging copy). */
 int scl_wrap_device(scl_ctx* ctx, void* dev0, void* dev1, scl_dtype dtype,
                     uint64_t n, scl_part* out);
+
+/* Refresh a resident partition with new host data of the same length (the
+ * data side of mapParameters for the next task on the same buffers,
+ * Sec. 3.1.1.1): host0[n] (and host1[n] for keyed) are copied into the
+ * partition's device arrays on `stream`; nothing is allocated.  With pinned
+ * host memory the copy is asynchronous: keep the host arrays unchanged until
+ * the stream reaches it.  Works for library-owned and wrapped partitions. */
+int scl_reload_partition(scl_ctx* ctx, scl_part part, const void* host0,
+                         const void* host1, void* stream);
 
 /* Release a partition (returns its arena block if the library owns it). */
 int scl_free_partition(scl_ctx* ctx, scl_part part);

@@ -227,6 +227,19 @@ int scl_wrap_device(scl_ctx* ctx, void* dev0, void* dev1, scl_dtype dtype, uint6
     return SCL_OK;
 }
 
+int scl_reload_partition(scl_ctx* ctx, scl_part part, const void* host0, const void* host1,
+                         void* stream) {
+    CTX_ENTER(ctx);
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (!p->n) return SCL_OK;
+    if (!host0 || (p->d1 && !host1)) return fail(SCL_E_INVALID, "null host array");
+    SCL_CUDA(cudaMemcpyAsync(p->d0, host0, p->n * 4, cudaMemcpyHostToDevice, S(stream)));
+    if (p->d1)
+        SCL_CUDA(cudaMemcpyAsync(p->d1, host1, p->n * 4, cudaMemcpyHostToDevice, S(stream)));
+    return SCL_OK;
+}
+
 int scl_free_partition(scl_ctx* ctx, scl_part part) {
     CTX_ENTER(ctx);
     auto it = ctx->parts.find(part);

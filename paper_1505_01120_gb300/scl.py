@@ -135,6 +135,7 @@ _SIGS = {
     "scl_load_partition_kv": ([_P, _P, _P, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_wrap_device": ([_P, _P, _P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_free_partition": ([_P, _u64], ctypes.c_int),
+    "scl_reload_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
     "scl_partition_info": ([_P, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
                             _PP, _PP], ctypes.c_int),
     "scl_read_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
@@ -266,6 +267,10 @@ def scl_wrap_device(ctx: int, dev0, dev1, dtype: int, n: int) -> int:
     out = _u64()
     _check(lib.scl_wrap_device(ctx, _ptr(dev0), _ptr(dev1), dtype, n, ctypes.byref(out)))
     return out.value
+
+
+def scl_reload_partition(ctx: int, part: int, host0, host1=None, stream: int = 0) -> None:
+    _check(lib.scl_reload_partition(ctx, part, _ptr(host0), _ptr(host1), stream))
 
 
 def scl_free_partition(ctx: int, part: int) -> None:
