@@ -18,6 +18,8 @@ passage of the SparkCL paper (Segal et al. 2015) it follows:
 * ``keyed_count_sum`` -- the WordCount-style reduce-by-key (Sec. 3.2.3).
 * ``combine`` / ``combine_keyed`` -- ReduceCL's tree combine of per-partition
   results (Sec. 3.1.3 item 3, Sec. 3.2.2), as a plain left fold.
+* ``add_arrays`` -- ReduceCL over k partition arrays with the vector-add
+  kernel of Fig. 3 (Sec. 3.2.2), in the binary-counter tree order.
 """
 from __future__ import annotations
 
@@ -66,6 +68,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_combine.restype = None
     lib.orc_combine_keyed.argtypes = [P, P, u32, u32, P, P]
     lib.orc_combine_keyed.restype = None
+    lib.orc_add_arrays_f32.argtypes = [P, u32, u64, P]
+    lib.orc_add_arrays_f32.restype = None
+    lib.orc_add_arrays_u32.argtypes = [P, u32, u64, P]
+    lib.orc_add_arrays_u32.restype = None
     return lib
 
 
@@ -194,3 +200,26 @@ def combine_keyed(counts, sums, lib=None):
     so = np.empty(nk, dtype=np.float64)
     (lib or load()).orc_combine_keyed(_ptr(c), _ptr(s), k, nk, _ptr(co), _ptr(so))
     return co, so
+
+
+def add_arrays(arrays, lib=None) -> np.ndarray:
+    """ReduceCL of k equal-length fp32 or uint32 arrays with the Fig. 3 vector-add
+    kernel (Sec. 3.2.2): fp32 in the binary-counter tree order, uint32 wrapping."""
+    arrays = list(arrays)
+    if not arrays:
+        raise ValueError("need at least one array")
+    if len(arrays) > 4096:
+        raise ValueError("at most 4096 arrays")
+    dt = np.asarray(arrays[0]).dtype
+    if dt not in (np.float32, np.uint32):
+        raise ValueError("fp32 or uint32 arrays")
+    arrs = [np.ascontiguousarray(a, dtype=dt) for a in arrays]
+    n = arrs[0].size
+    if any(a.size != n for a in arrs):
+        raise ValueError("arrays differ in length")
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    out = np.empty(n, dtype=dt)
+    fn = (lib or load()).orc_add_arrays_f32 if dt == np.float32 else \
+        (lib or load()).orc_add_arrays_u32
+    fn(ctypes.cast(ptrs, ctypes.c_void_p), len(arrs), n, out.ctypes.data)
+    return out

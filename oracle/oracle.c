@@ -24,7 +24,15 @@
  *            t = fma(a, x*x, b); y = fma(t, x, c) with x*x rounded once,
  *            coefficients {a, b, c} = {0.5f, -1.25f, 0.1f} by default;
  *   keyed  : count[key] += 1, sum[key] += value over (int32 key, fp32 value)
- *            pairs, keys in [0, num_keys).
+ *            pairs, keys in [0, num_keys);
+ *   add    : the vector-add kernel of Fig. 3, c[gid] = a[gid] + b[gid], used by
+ *            ReduceCL to fold k equal-length partition arrays with a tree
+ *            reduce (Sec. 3.2.2).  The tree is the binary-counter tree:
+ *            leaves are taken left to right; whenever the two newest subtrees
+ *            hold the same number of leaves they are combined (older + newer);
+ *            after the last leaf the remaining subtrees are combined from the
+ *            newest to the oldest, each older one on the left.  For k a power
+ *            of two this is the balanced pairwise tree.
  * Accumulation is fp64 for floating point (the method's reference precision)
  * and exact uint64 (mod 2^64) for integers.  Min/max ignore NaN (a NaN never
  * replaces a number); an empty partition has sum 0, min +inf, max -inf.
@@ -138,6 +146,58 @@ uint64_t orc_keyed_count_sum(const int32_t *keys, const float *vals, uint64_t n,
         sum[k] += (double)vals[i];
     }
     return bad;
+}
+
+/* --------------------------------------- ReduceCL over partition arrays */
+
+/* One output element of the tree reduce of k fp32 values x[0..k-1] (fp32
+ * adds in the binary-counter tree order described at the top).  The stack
+ * holds one subtree per set bit of the number of leaves seen so far, the
+ * oldest (largest) at the bottom. */
+static float tree_sum_f32(const float *x, uint32_t k)
+{
+    float stack[64];
+    uint32_t size[64];
+    uint32_t top = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+        stack[top] = x[j];
+        size[top] = 1;
+        ++top;
+        while (top >= 2 && size[top - 2] == size[top - 1]) {
+            stack[top - 2] = stack[top - 2] + stack[top - 1];   /* older + newer */
+            size[top - 2] += size[top - 1];
+            --top;
+        }
+    }
+    if (top == 0)
+        return 0.0f;
+    float acc = stack[top - 1];
+    for (uint32_t i = top - 1; i-- > 0;)
+        acc = stack[i] + acc;                                    /* older on the left */
+    return acc;
+}
+
+/* ReduceCL of k fp32 partition arrays of n elements each (Sec. 3.2.2 with the
+ * Fig. 3 kernel): out[i] = tree sum over j of arrays[j][i].  k >= 1. */
+void orc_add_arrays_f32(const float *const *arrays, uint32_t k, uint64_t n, float *out)
+{
+    float col[4096];
+    for (uint64_t i = 0; i < n; ++i) {
+        for (uint32_t j = 0; j < k; ++j)
+            col[j] = arrays[j][i];
+        out[i] = tree_sum_f32(col, k);
+    }
+}
+
+/* The same for uint32 arrays: wrapping addition mod 2^32 (order-free). */
+void orc_add_arrays_u32(const uint32_t *const *arrays, uint32_t k, uint64_t n, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t s = 0;
+        for (uint32_t j = 0; j < k; ++j)
+            s += arrays[j][i];
+        out[i] = s;
+    }
 }
 
 /* ---------------------------------------------- combine across partitions */

@@ -53,6 +53,17 @@ MUTATIONS = [
      "sum[k] += (double)vals[i ? i - 1 : 0];", ["keyed_against_bincount"]),
     ("keyed_accepts_last_bad_key", "(uint32_t)k >= num_keys", "(uint32_t)k > num_keys",
      ["keyed_special_cases"]),
+    ("tree_as_left_fold", "while (top >= 2 && size[top - 2] == size[top - 1]) {",
+     "while (top >= 2) {", ["add_arrays", "add_arrays_tree_shape"]),
+    ("tree_final_fold_oldest_first",
+     "float acc = stack[top - 1];\n    for (uint32_t i = top - 1; i-- > 0;)\n        acc = stack[i] + acc;",
+     "float acc = stack[0];\n    for (uint32_t i = 1; i < top; ++i)\n        acc = acc + stack[i];",
+     ["add_arrays_tree_shape"]),
+    ("add_drops_last_array", "for (uint32_t j = 0; j < k; ++j)\n            col[j] = arrays[j][i];\n        out[i] = tree_sum_f32(col, k);",
+     "for (uint32_t j = 0; j < k; ++j)\n            col[j] = arrays[j][i];\n        out[i] = tree_sum_f32(col, k - 1);",
+     ["add_arrays"]),
+    ("u32_add_drops_array", "for (uint32_t j = 0; j < k; ++j)\n            s += arrays[j][i];",
+     "for (uint32_t j = 1; j < k; ++j)\n            s += arrays[j][i];", ["add_arrays"]),
     ("combine_first_only", "us += u64_sums[i];", "us += u64_sums[0];",
      ["combine_equals_whole"]),
     ("combine_keyed_transposed", "c += counts[(uint64_t)i * num_keys + j];",

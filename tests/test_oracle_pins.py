@@ -260,6 +260,54 @@ def pin_combine_equals_whole(lib):
     assert np.allclose(so, sw, rtol=1e-9, atol=1e-9)
 
 
+def pin_add_arrays(lib):
+    """The tree reduce of k arrays: k = 1 is the identity; k = 2 is one fp32
+    add (numpy's np.add rounds once); k a power of two is the balanced pairwise
+    tree, computed level by level by numpy; for any k, arrays of small integers
+    (exact in fp32) sum to numpy's exact total; uint32 wraps mod 2^32."""
+    rng = np.random.default_rng(21)
+    n = 1000
+    xs = [rng.standard_normal(n, dtype=np.float32) * (j + 1) for j in range(33)]
+    assert np.array_equal(oracle.add_arrays(xs[:1], lib=lib), xs[0])
+    assert np.array_equal(oracle.add_arrays(xs[:2], lib=lib).view(np.uint32),
+                          np.add(xs[0], xs[1]).view(np.uint32))
+    for k in (4, 8, 16, 32):
+        lev = np.stack(xs[:k])
+        while lev.shape[0] > 1:
+            lev = lev[0::2] + lev[1::2]          # fp32 adds, adjacent pairs
+        assert np.array_equal(oracle.add_arrays(xs[:k], lib=lib).view(np.uint32),
+                              lev[0].view(np.uint32)), k
+    for k in (3, 5, 7, 13, 33):
+        ints = [rng.integers(-1000, 1000, size=n).astype(np.float32) for _ in range(k)]
+        assert np.array_equal(oracle.add_arrays(ints, lib=lib),
+                              np.sum(np.stack(ints), axis=0, dtype=np.float64).astype(np.float32))
+        got = oracle.add_arrays(xs[:k], lib=lib).astype(np.float64)
+        exact = np.array([math.fsum(float(x[i]) for x in xs[:k]) for i in range(n)])
+        scale = np.sum(np.abs(np.stack(xs[:k]).astype(np.float64)), axis=0)
+        assert np.all(np.abs(got - exact) <= k * 2.0 ** -24 * scale)
+    us = [rng.integers(0, 1 << 32, size=n, dtype=np.uint32) for _ in range(9)]
+    want = np.array([sum(int(u[i]) for u in us) % (1 << 32) for i in range(n)], np.uint32)
+    assert np.array_equal(oracle.add_arrays(us, lib=lib), want)
+
+
+def pin_add_arrays_tree_shape(lib):
+    """Non-power-of-two k: the binary-counter tree for k = 3 is x0 + ... taken
+    as (x0 + x1) + x2, and for k = 6 as ((x0+x1)+(x2+x3)) + (x4+x5).  Values are
+    chosen so a different association rounds differently."""
+    big, one = np.float32(2.0 ** 24), np.float32(1.0)
+    a = [np.array([v], np.float32) for v in (big, one, one)]
+    # (2^24 + 1) rounds to 2^24, then + 1 rounds to 2^24 again
+    assert oracle.add_arrays(a, lib=lib)[0] == big
+    b = [np.array([v], np.float32) for v in (one, one, one, one, big, one)]
+    # ((1+1)+(1+1)) + (2^24+1) = 4 + 2^24 -> 2^24 + 4
+    assert oracle.add_arrays(b, lib=lib)[0] == big + np.float32(4.0)
+    zero = np.float32(0.0)
+    c = [np.array([v], np.float32) for v in (big, zero, zero, zero, one, zero, one)]
+    # k = 7 leaves three subtrees of 4, 2 and 1 leaves: 2^24 + ((1+0) + 1) is
+    # 2^24 + 2, while (2^24 + 1) + 1 would round to 2^24 twice
+    assert oracle.add_arrays(c, lib=lib)[0] == big + np.float32(2.0)
+
+
 PINS = {
     "mix32_left_inverse": pin_mix32_left_inverse,
     "mix32_full_domain_sum": pin_mix32_full_domain_sum,
@@ -273,6 +321,8 @@ PINS = {
     "keyed_against_bincount": pin_keyed_against_bincount,
     "keyed_special_cases": pin_keyed_special_cases,
     "combine_equals_whole": pin_combine_equals_whole,
+    "add_arrays": pin_add_arrays,
+    "add_arrays_tree_shape": pin_add_arrays_tree_shape,
 }
 
 
