@@ -318,6 +318,7 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
         scl.scl_free_partition(ctx.handle, q)
     del dk, dv, outs
 
+    out["vector_add_reduce_64x4194304"] = vector_add_config(torch, scl, ctx, stream, pk)
     out["batch_10000"] = batch_config(torch, scl, ctx, stream)
     out["serve"] = serve_config(torch, scl, ctx, stream, full)
     return out
@@ -397,6 +398,34 @@ def serve_config(torch, scl, ctx, stream, full: bool) -> dict:
     for t in tasks:
         scl.scl_free_partition(ctx.handle, t["part"])
     return out
+
+
+def vector_add_config(torch, scl, ctx, stream, pk: float) -> dict:
+    """ReduceCL over 64 fp32 partition arrays of 4,194,304 with the Fig. 3
+    vector-add kernel: one pass reads the 64 arrays and writes the tree sum."""
+    import oracle
+    st = stream.cuda_stream
+    k, n = 64, 1 << 22
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6)
+    x = torch.randn(k * n, device="cuda", generator=g)
+    parts = [scl.scl_wrap_device(ctx.handle, x.data_ptr() + j * n * 4, None, scl.SCL_F32, n)
+             for j in range(k)]
+    out = scl.scl_reduce_arrays(ctx.handle, parts, stream=st)
+    ms = time_device(torch, stream, lambda: scl.scl_reduce_arrays_into(ctx.handle, parts, out,
+                                                                       stream=st), 20)
+    nbytes = (k + 1) * n * 4
+    got = np.empty(n, np.float32)
+    scl.scl_read_partition(ctx.handle, out, got, stream=st)
+    lo = n // 2
+    cols = x.view(k, n)[:, lo:lo + 4096].cpu().numpy()
+    want = oracle.add_arrays(list(cols))
+    exact = bool(np.array_equal(got[lo:lo + 4096].view(np.uint32), want.view(np.uint32)))
+    for p in parts + [out]:
+        scl.scl_free_partition(ctx.handle, p)
+    del x
+    return {"gbs": nbytes / ms / 1e6, "frac_of_hbm": nbytes / ms / 1e6 / pk, "ms": ms,
+            "bytes": nbytes, "sampled_4096_bit_exact_vs_oracle": exact}
 
 
 def batch_config(torch, scl, ctx, stream) -> dict:

@@ -266,6 +266,37 @@ int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,
                            void* stream, uint32_t* counts_out, float* sums_out,
                            double* sums64_out, scl_result* dev_result);
 
+/* ------------------------------------- ReduceCL over partition arrays (Fig. 3) */
+
+/* Largest number of arrays scl_reduce_arrays folds in one call. */
+#define SCL_MAX_REDUCE_ARRAYS 1024
+
+/* The paper's worked example (Fig. 3, Sec. 3.2.2 VectorAdd): the binary
+ * kernel c[gid] = a[gid] + b[gid] used by ReduceCL, which folds the arrays of
+ * an RDD's elements with a tree reduce.  scl_reduce_arrays folds k
+ * equal-length partition arrays in one pass: out[i] = the tree sum of
+ * parts[0][i] .. parts[k-1][i].  The tree is the binary-counter tree: arrays
+ * are taken in order; whenever the two newest subtrees hold the same number
+ * of arrays they are combined (older + newer); the leftover subtrees are
+ * combined newest first, each older one on the left (the balanced pairwise
+ * tree when k is a power of two).  F32: fp32 adds in that order, so results
+ * are bitwise reproducible; U32/I32: addition mod 2^32.
+ *
+ * All partitions must have the same length and dtype class (F32, or 32-bit
+ * integers); 1 <= k <= SCL_MAX_REDUCE_ARRAYS.  Enqueued on `stream`.
+ * scl_reduce_arrays allocates the output partition (dtype of parts[0]);
+ * scl_reduce_arrays_into writes an existing partition of the same length and
+ * allocates nothing.  Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED (keyed),
+ * SCL_E_NOMEM. */
+int scl_reduce_arrays(scl_ctx* ctx, const scl_part* parts, uint32_t k, void* stream,
+                      scl_part* out);
+int scl_reduce_arrays_into(scl_ctx* ctx, const scl_part* parts, uint32_t k,
+                           scl_part out, void* stream);
+
+/* One step of Fig. 3 itself: c = a + b elementwise (scl_reduce_arrays with
+ * k = 2). */
+int scl_vector_add(scl_ctx* ctx, scl_part a, scl_part b, void* stream, scl_part* out);
+
 /* ----------------------------------------------- ReduceCL across partitions */
 
 /* Host tree-combine of k per-partition results (ReduceCL's treeReduce,

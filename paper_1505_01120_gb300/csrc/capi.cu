@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "runtime.h"
 #include "server.h"
@@ -411,6 +412,91 @@ int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys, void*
     if (!counts_out || !sums_out) return fail(SCL_E_INVALID, "null output table");
     return keyed_common(ctx, part, num_keys, stream, counts_out, sums_out, sums64_out,
                         dev_result ? dev_result : ctx->d_result);
+}
+
+// ------------------------------------------------ ReduceCL over arrays
+
+static bool int_class(scl_dtype d) { return d == SCL_U32 || d == SCL_I32; }
+
+static int check_arrays(scl_ctx* ctx, const scl_part* parts, uint32_t k,
+                        std::vector<Partition>* ps) {
+    if (!parts || k < 1 || k > kMaxTreeArrays)
+        return fail(SCL_E_INVALID, "need 1..%u partitions", kMaxTreeArrays);
+    ps->resize(k);
+    for (uint32_t j = 0; j < k; ++j) {
+        const Partition* p = ctx->part(parts[j]);
+        if (!p) return fail(SCL_E_INVALID, "partition %u: unknown handle", j);
+        if (p->dtype == SCL_KV_I32_F32)
+            return fail(SCL_E_UNSUPPORTED, "keyed partitions cannot be added elementwise");
+        (*ps)[j] = *p;
+        if (p->n != (*ps)[0].n) return fail(SCL_E_INVALID, "partition %u differs in length", j);
+        if (int_class(p->dtype) != int_class((*ps)[0].dtype))
+            return fail(SCL_E_INVALID, "partition %u differs in dtype class", j);
+    }
+    return SCL_OK;
+}
+
+static int launch_tree_add(scl_ctx* ctx, const std::vector<Partition>& ps, void* out,
+                           cudaStream_t st) {
+    const uint64_t n = ps[0].n;
+    if (!n) return SCL_OK;
+    TreeArgs a;
+    memset(&a, 0, sizeof a);
+    bool aligned = ((uintptr_t)out % 16) == 0;
+    for (size_t j = 0; j < ps.size(); ++j) {
+        a.in[j] = static_cast<const char*>(ps[j].d0);
+        aligned = aligned && ((uintptr_t)ps[j].d0 % 16) == 0;
+    }
+    a.out = static_cast<char*>(out);
+    a.n = n;
+    a.k = (uint32_t)ps.size();
+    const int f32 = ps[0].dtype == SCL_F32;
+    const void* fn = tree_add_kernel_fn(f32, aligned, a.k);
+    int nb = 0;
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0));
+    const uint64_t work = aligned ? (n + 3) / 4 : n;
+    const uint64_t want = (work + 255) / 256;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(want, (uint64_t)ctx->sms * std::max(nb, 1)));
+    void* params[] = {&a};
+    SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(256), params, 0, st));
+    count_launches(1);
+    return SCL_OK;
+}
+
+int scl_reduce_arrays_into(scl_ctx* ctx, const scl_part* parts, uint32_t k, scl_part out,
+                           void* stream) {
+    CTX_ENTER(ctx);
+    std::vector<Partition> ps;
+    SCL_TRY(check_arrays(ctx, parts, k, &ps));
+    const Partition* o = ctx->part(out);
+    if (!o) return fail(SCL_E_INVALID, "unknown output partition");
+    if (o->n != ps[0].n || o->dtype == SCL_KV_I32_F32 ||
+        int_class(o->dtype) != int_class(ps[0].dtype))
+        return fail(SCL_E_INVALID, "output partition must match the inputs' length and dtype");
+    return launch_tree_add(ctx, ps, o->d0, S(stream));
+}
+
+int scl_reduce_arrays(scl_ctx* ctx, const scl_part* parts, uint32_t k, void* stream,
+                      scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    std::vector<Partition> ps;
+    SCL_TRY(check_arrays(ctx, parts, k, &ps));
+    Partition o;
+    SCL_TRY(new_partition(ctx, ps[0].dtype, ps[0].n, &o));
+    const int st = launch_tree_add(ctx, ps, o.d0, S(stream));
+    if (st != SCL_OK) {
+        ctx->arena.release(o.block);
+        return st;
+    }
+    *out = register_partition(ctx, o);
+    return SCL_OK;
+}
+
+int scl_vector_add(scl_ctx* ctx, scl_part a, scl_part b, void* stream, scl_part* out) {
+    const scl_part parts[2] = {a, b};
+    return scl_reduce_arrays(ctx, parts, 2, stream, out);
 }
 
 // ----------------------------------------------------------------- combine

@@ -136,6 +136,19 @@ __host__ __device__ inline uint32_t keyed_single_pieces(uint64_t n, uint32_t gri
     return (uint32_t)g;
 }
 
+// ReduceCL over k equal-length partition arrays (the vector-add kernel of
+// Fig. 3 folded by a tree reduce, Sec. 3.2.2).
+constexpr uint32_t kMaxTreeArrays = 1024;
+constexpr int kTreeLevels = 11;                     // 2^10 leaves need 11 levels
+
+struct TreeArgs {
+    const char* in[kMaxTreeArrays];   // device addresses of the k input arrays
+    char* out;
+    uint64_t n;                       // elements per array
+    uint32_t k;
+    uint32_t pad;
+};
+
 // Host-side launch entry of one compiled persistent-kernel instantiation.
 struct KernelEntry {
     int mask, block, ipt;              // block = threads that touch data (consumers)
@@ -155,5 +168,6 @@ extern const void* fold_kernel_fn();
 extern const void* map_kernel_fn(int kind, int aligned);
 extern int map_kernel_block();
 extern int map_kernel_ipt();
+extern const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k);
 
 }  // namespace scl

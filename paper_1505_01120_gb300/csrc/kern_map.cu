@@ -29,4 +29,14 @@ const void* map_kernel_fn(int kind, int aligned) {
     }
 }
 
+// Stack depth 7 holds up to 127 arrays, 11 up to 2047 (kMaxTreeArrays = 1024).
+const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k) {
+    const bool small = k < 128;
+#define SCL_TREE(F, A) (small ? (const void*)&dev::k_tree_add<F, A, 7>   \
+                              : (const void*)&dev::k_tree_add<F, A, kTreeLevels>)
+    if (f32) return aligned ? SCL_TREE(true, true) : SCL_TREE(true, false);
+    return aligned ? SCL_TREE(false, true) : SCL_TREE(false, false);
+#undef SCL_TREE
+}
+
 }  // namespace scl

@@ -570,6 +570,94 @@ __global__ void __launch_bounds__(BLOCK) k_map(const void* in, void* out, uint64
     }
 }
 
+// ------------------------------------------------- tree add of k arrays
+
+template <bool F32>
+__device__ __forceinline__ uint32_t add1(uint32_t a, uint32_t b) {
+    if constexpr (F32) return __float_as_uint(__fadd_rn(__uint_as_float(a), __uint_as_float(b)));
+    else return a + b;
+}
+
+template <bool F32>
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b) {
+    return make_uint4(add1<F32>(a.x, b.x), add1<F32>(a.y, b.y), add1<F32>(a.z, b.z),
+                      add1<F32>(a.w, b.w));
+}
+
+// Binary-counter tree: level L holds a complete subtree of 2^L leaves exactly
+// when bit L of the leaf count is set.  Pushing a leaf carries it upward,
+// combining (older level value) + (newer carry), like an increment.
+template <bool F32, int LV, typename V>
+__device__ __forceinline__ void tree_push(V (&st)[LV], uint32_t& cnt, V x) {
+    bool carry = true;   // no early exit: every st[L] index stays a constant
+#pragma unroll
+    for (int L = 0; L < LV; ++L) {
+        const bool occupied = (cnt >> L) & 1u;
+        if (carry && occupied) {
+            if constexpr (sizeof(V) == 16) x = add4<F32>(st[L], x);
+            else x = add1<F32>(st[L], x);
+        } else if (carry) {
+            st[L] = x;
+            carry = false;
+        }
+    }
+    ++cnt;
+}
+
+// Leftover subtrees are combined newest (lowest level) first, each older one
+// on the left.
+template <bool F32, int LV, typename V>
+__device__ __forceinline__ V tree_finish(const V (&st)[LV], uint32_t cnt) {
+    V acc{};
+    bool have = false;
+#pragma unroll
+    for (int L = 0; L < LV; ++L) {
+        if (cnt & (1u << L)) {
+            if (!have) {
+                acc = st[L];
+                have = true;
+            } else if constexpr (sizeof(V) == 16) {
+                acc = add4<F32>(st[L], acc);
+            } else {
+                acc = add1<F32>(st[L], acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// out[i] = tree sum over j < k of in[j][i].  Grid-stride over 128-bit vectors
+// (ALIGNED: every array 16-byte aligned), then over the scalar remainder.
+// LV stack levels hold up to 2^LV - 1 arrays.
+template <bool F32, bool ALIGNED, int LV>
+__global__ void __launch_bounds__(256) k_tree_add(const __grid_constant__ TreeArgs a) {
+    const uint64_t nv = ALIGNED ? a.n / 4 : 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t k = a.k;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+        uint4 st[LV];
+        uint32_t cnt = 0;
+        uint32_t j = 0;
+        for (; j + 4 <= k; j += 4) {
+            uint4 x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = ld_stream_v4(a.in[j + q] + v * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tree_push<F32, LV>(st, cnt, x[q]);
+        }
+        for (; j < k; ++j) tree_push<F32, LV>(st, cnt, ld_stream_v4(a.in[j] + v * 16));
+        st_stream_v4(a.out + v * 16, tree_finish<F32, LV>(st, cnt));
+    }
+    for (uint64_t i = nv * 4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+         i += stride) {
+        uint32_t st[LV];
+        uint32_t cnt = 0;
+        for (uint32_t j = 0; j < k; ++j)
+            tree_push<F32, LV>(st, cnt, ld_stream_b32(a.in[j] + i * 4));
+        reinterpret_cast<uint32_t*>(a.out)[i] = tree_finish<F32, LV>(st, cnt);
+    }
+}
+
 }  // namespace dev
 }  // namespace scl
 

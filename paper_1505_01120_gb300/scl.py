@@ -36,6 +36,7 @@ SCL_K_IDENT, SCL_K_MIX32, SCL_K_POLY3 = 0, 1, 2
 # scl_reduce
 SCL_R_NONE, SCL_R_SUM, SCL_R_SUM_MIN_MAX, SCL_R_KEYED_COUNT_SUM = 0, 1, 2, 3
 SCL_NOALLOC_MAX_ELEMENTS = 67_108_864
+SCL_MAX_REDUCE_ARRAYS = 1024
 
 
 class scl_config(ctypes.Structure):
@@ -146,6 +147,9 @@ _SIGS = {
     "scl_keyed_reduce": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
                          ctypes.c_int),
     "scl_keyed_reduce_async": ([_P, _u64, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "scl_reduce_arrays": ([_P, _P, _u32, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_reduce_arrays_into": ([_P, _P, _u32, _u64, _P], ctypes.c_int),
+    "scl_vector_add": ([_P, _u64, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_combine": ([_P, _u32, ctypes.POINTER(scl_result)], ctypes.c_int),
     "scl_combine_keyed": ([_P, _P, _u32, _u32, _P, _P], ctypes.c_int),
     "scl_batch_create": ([_P, _P, _u32, _PP], ctypes.c_int),
@@ -332,6 +336,28 @@ def scl_keyed_reduce_async(ctx: int, part: int, num_keys: int, counts_dev, sums_
                            sums64_dev=None, result_dev=None, stream: int = 0) -> None:
     _check(lib.scl_keyed_reduce_async(ctx, part, num_keys, stream, _ptr(counts_dev),
                                       _ptr(sums_dev), _ptr(sums64_dev), _ptr(result_dev)))
+
+
+def _parts(parts) -> ctypes.Array:
+    return (ctypes.c_uint64 * max(1, len(parts)))(*parts)
+
+
+def scl_reduce_arrays(ctx: int, parts, stream: int = 0) -> int:
+    out = _u64()
+    _check(lib.scl_reduce_arrays(ctx, ctypes.cast(_parts(parts), ctypes.c_void_p), len(parts),
+                                 stream, ctypes.byref(out)))
+    return out.value
+
+
+def scl_reduce_arrays_into(ctx: int, parts, out: int, stream: int = 0) -> None:
+    _check(lib.scl_reduce_arrays_into(ctx, ctypes.cast(_parts(parts), ctypes.c_void_p),
+                                      len(parts), out, stream))
+
+
+def scl_vector_add(ctx: int, a: int, b: int, stream: int = 0) -> int:
+    out = _u64()
+    _check(lib.scl_vector_add(ctx, a, b, stream, ctypes.byref(out)))
+    return out.value
 
 
 def scl_combine(parts) -> scl_result:
