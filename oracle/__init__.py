@@ -15,7 +15,8 @@ passage of the SparkCL paper (Segal et al. 2015) it follows:
   (Sec. 3.1.3 item 3).
 * ``poly3`` / ``map_poly3`` / ``reduce_f32`` -- the fp32 user kernel
   (MapCLPartition, Sec. 3.1.3 item 2) with ReduceCL's sum/min/max.
-* ``keyed_count_sum`` -- the WordCount-style reduce-by-key (Sec. 3.2.3).
+* ``keyed_count_sum`` -- the WordCount-style reduce-by-key (Sec. 3.2.3);
+  ``keyed_hashed_count_sum`` the same after hashing each key into a bucket.
 * ``combine`` / ``combine_keyed`` -- ReduceCL's tree combine of per-partition
   results (Sec. 3.1.3 item 3, Sec. 3.2.2), as a plain left fold.
 * ``add_arrays`` -- ReduceCL over k partition arrays with the vector-add
@@ -68,6 +69,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_combine.restype = None
     lib.orc_combine_keyed.argtypes = [P, P, u32, u32, P, P]
     lib.orc_combine_keyed.restype = None
+    lib.orc_keyed_hashed_count_sum.argtypes = [P, P, u64, u32, P, P]
+    lib.orc_keyed_hashed_count_sum.restype = None
     lib.orc_add_arrays_f32.argtypes = [P, u32, u64, P]
     lib.orc_add_arrays_f32.restype = None
     lib.orc_add_arrays_u32.argtypes = [P, u32, u64, P]
@@ -169,6 +172,20 @@ def keyed_count_sum(keys, vals, num_keys: int = 4096, lib=None):
     bad = (lib or load()).orc_keyed_count_sum(_ptr(keys), _ptr(vals), keys.size,
                                               num_keys, _ptr(cnt), _ptr(s))
     return cnt, s, int(bad)
+
+
+def keyed_hashed_count_sum(keys, vals, num_keys: int = 4096, lib=None):
+    """Reduce-by-key after hashing each key into a bucket,
+    (mix32(key) * num_keys) >> 32 (Sec. 3.2.3): (uint32 count, fp64 sum)."""
+    keys = _c(keys, np.int32)
+    vals = _c(vals, np.float32)
+    if keys.size != vals.size:
+        raise ValueError("keys and vals differ in length")
+    cnt = np.empty(num_keys, dtype=np.uint32)
+    s = np.empty(num_keys, dtype=np.float64)
+    (lib or load()).orc_keyed_hashed_count_sum(_ptr(keys), _ptr(vals), keys.size, num_keys,
+                                               _ptr(cnt), _ptr(s))
+    return cnt, s
 
 
 def combine(u64_sums, f64_sums, mins, maxs, lib=None):

@@ -25,6 +25,9 @@
  *            coefficients {a, b, c} = {0.5f, -1.25f, 0.1f} by default;
  *   keyed  : count[key] += 1, sum[key] += value over (int32 key, fp32 value)
  *            pairs, keys in [0, num_keys);
+ *   hashed keyed: the keyed reduce with each key first mixed by mix32 and
+ *            mapped into [0, num_keys) as (mix32(key) * num_keys) >> 32
+ *            (a WordCount-style hash into buckets, Sec. 3.2.3);
  *   add    : the vector-add kernel of Fig. 3, c[gid] = a[gid] + b[gid], used by
  *            ReduceCL to fold k equal-length partition arrays with a tree
  *            reduce (Sec. 3.2.2).  The tree is the binary-counter tree:
@@ -146,6 +149,23 @@ uint64_t orc_keyed_count_sum(const int32_t *keys, const float *vals, uint64_t n,
         sum[k] += (double)vals[i];
     }
     return bad;
+}
+
+/* Keyed reduce with hashed keys: bucket = (mix32(key) * num_keys) >> 32,
+ * computed in 64-bit, so every 32-bit key lands in [0, num_keys).  Outputs
+ * are overwritten; num_keys >= 1. */
+void orc_keyed_hashed_count_sum(const int32_t *keys, const float *vals, uint64_t n,
+                                uint32_t num_keys, uint32_t *count, double *sum)
+{
+    memset(count, 0, sizeof(uint32_t) * num_keys);
+    for (uint32_t k = 0; k < num_keys; ++k)
+        sum[k] = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t h = orc_mix32((uint32_t)keys[i]);
+        uint32_t b = (uint32_t)(((uint64_t)h * num_keys) >> 32);
+        count[b] += 1u;
+        sum[b] += (double)vals[i];
+    }
 }
 
 /* --------------------------------------- ReduceCL over partition arrays */

@@ -53,6 +53,10 @@ MUTATIONS = [
      "sum[k] += (double)vals[i ? i - 1 : 0];", ["keyed_against_bincount"]),
     ("keyed_accepts_last_bad_key", "(uint32_t)k >= num_keys", "(uint32_t)k > num_keys",
      ["keyed_special_cases"]),
+    ("hash_bucket_by_low_bits", "uint32_t b = (uint32_t)(((uint64_t)h * num_keys) >> 32);",
+     "uint32_t b = h % num_keys;", ["keyed_hashed"]),
+    ("hash_bucket_unmixed", "uint32_t h = orc_mix32((uint32_t)keys[i]);",
+     "uint32_t h = (uint32_t)keys[i];", ["keyed_hashed"]),
     ("tree_as_left_fold", "while (top >= 2 && size[top - 2] == size[top - 1]) {",
      "while (top >= 2) {", ["add_arrays", "add_arrays_tree_shape"]),
     ("tree_final_fold_oldest_first",

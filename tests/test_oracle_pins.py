@@ -260,6 +260,30 @@ def pin_combine_equals_whole(lib):
     assert np.allclose(so, sw, rtol=1e-9, atol=1e-9)
 
 
+def pin_keyed_hashed(lib):
+    """Hashed buckets: for num_keys = 2^m the bucket is the top m bits of mix32
+    (multiply-high by a power of two is a shift), with mix32 itself pinned by its
+    inverse; for any num_keys, bucket counts/sums equal numpy bincount over the
+    buckets computed with Python integers, and every pair is counted."""
+    rng = np.random.default_rng(22)
+    keys = rng.integers(-2**31, 2**31, size=60_000, dtype=np.int32)
+    vals = rng.random(60_000, dtype=np.float32)
+    mixed = oracle.map_mix32(keys.view(np.uint32), lib=lib)
+    assert np.array_equal(unmix32(mixed), keys.view(np.uint32))
+    for m in (0, 1, 6, 12):
+        nk = 1 << m
+        cnt, s = oracle.keyed_hashed_count_sum(keys, vals, nk, lib=lib)
+        b = (mixed >> np.uint32(32 - m)).astype(np.int64) if m else np.zeros(keys.size, np.int64)
+        assert np.array_equal(cnt, np.bincount(b, minlength=nk).astype(np.uint32)), m
+        assert np.allclose(s, np.bincount(b, weights=vals.astype(np.float64), minlength=nk),
+                           rtol=1e-12, atol=0)
+    for nk in (3, 1000, 4095):
+        cnt, s = oracle.keyed_hashed_count_sum(keys, vals, nk, lib=lib)
+        b = np.array([(int(h) * nk) >> 32 for h in mixed], np.int64)
+        assert np.array_equal(cnt, np.bincount(b, minlength=nk).astype(np.uint32)), nk
+        assert int(cnt.sum()) == keys.size
+
+
 def pin_add_arrays(lib):
     """The tree reduce of k arrays: k = 1 is the identity; k = 2 is one fp32
     add (numpy's np.add rounds once); k a power of two is the balanced pairwise
@@ -321,6 +345,7 @@ PINS = {
     "keyed_against_bincount": pin_keyed_against_bincount,
     "keyed_special_cases": pin_keyed_special_cases,
     "combine_equals_whole": pin_combine_equals_whole,
+    "keyed_hashed": pin_keyed_hashed,
     "add_arrays": pin_add_arrays,
     "add_arrays_tree_shape": pin_add_arrays_tree_shape,
 }
