@@ -318,6 +318,8 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
         scl.scl_free_partition(ctx.handle, q)
     del dk, dv, outs
 
+    out["keyed_hashed_count_sum_16x16777216"] = keyed_hashed_config(torch, scl, ctx, stream, pk)
+    out["map_materialised_268435456"] = map_config(torch, scl, ctx, stream, pk)
     out["vector_add_reduce_64x4194304"] = vector_add_config(torch, scl, ctx, stream, pk)
     out["batch_10000"] = batch_config(torch, scl, ctx, stream)
     out["serve"] = serve_config(torch, scl, ctx, stream, full)
@@ -397,6 +399,73 @@ def serve_config(torch, scl, ctx, stream, full: bool) -> dict:
         out["rates"][str(rate)] = row
     for t in tasks:
         scl.scl_free_partition(ctx.handle, t["part"])
+    return out
+
+
+def keyed_hashed_config(torch, scl, ctx, stream, pk: float) -> dict:
+    """Keyed count+sum with 32-bit keys hashed into 4096 buckets, 16 x 16 Mi pairs."""
+    import oracle
+    st = stream.cuda_stream
+    m = 1 << 24
+    rng = np.random.default_rng(7)
+    keys = synth.uniform_u32(16 * m, rng).view(np.int32)
+    vals = synth.unit_f32(16 * m, rng)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    outs = torch.zeros((16, 4096 * 4), dtype=torch.int32, device="cuda")
+    parts, tasks = [], []
+    for i in range(16):
+        q = scl.scl_wrap_device(ctx.handle, dk.data_ptr() + i * m * 4, dv.data_ptr() + i * m * 4,
+                                scl.SCL_KV_I32_F32, m)
+        parts.append(q)
+        base = outs[i].data_ptr()
+        tasks.append(dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                          num_keys=4096, counts_out=base, sums_out=base + 4096 * 4,
+                          sums64_out=base + 4096 * 8))
+    b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
+    scl.scl_batch_capture(b, st)
+    ms = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 20)
+    scl.scl_batch_results(b, 16, stream=st)
+    o0 = outs[0].cpu().numpy()
+    ocnt, osum = oracle.keyed_hashed_count_sum(keys[:m], vals[:m], 4096)
+    scl.scl_batch_destroy(b)
+    for q in parts:
+        scl.scl_free_partition(ctx.handle, q)
+    return {"gbs": 16 * m * 8 / ms / 1e6, "frac_of_hbm": 16 * m * 8 / ms / 1e6 / pk, "ms": ms,
+            "partition0_counts_exact": bool(np.array_equal(o0[:4096].view(np.uint32), ocnt)),
+            "partition0_max_rel_err": float(np.max(np.abs(o0[8192:].view(np.float64) - osum)
+                                                   / np.abs(osum)))}
+
+
+def map_config(torch, scl, ctx, stream, pk: float) -> dict:
+    """MapCL with the output array materialised: 256 Mi elements, 4 B read + 4 B
+    written per element, mix32 on uint32 and poly3 on fp32 (scl_map_into)."""
+    import oracle
+    st = stream.cuda_stream
+    n = 1 << 28
+    g = torch.Generator(device="cuda")
+    g.manual_seed(8)
+    x = torch.randn(n, device="cuda", generator=g)
+    y = torch.empty(n, device="cuda")
+    out = {}
+    for name, dt, kern in (("mix32", scl.SCL_U32, scl.SCL_K_MIX32),
+                           ("poly3", scl.SCL_F32, scl.SCL_K_POLY3)):
+        p = scl.scl_wrap_device(ctx.handle, x.data_ptr(), None, dt, n)
+        q = scl.scl_wrap_device(ctx.handle, y.data_ptr(), None, dt, n)
+        ms = time_device(torch, stream, lambda: scl.scl_map_into(ctx.handle, p, kern, q,
+                                                                 stream=st), 10)
+        torch.cuda.synchronize()
+        xs = x[: 1 << 16].cpu().numpy()
+        ys = y[: 1 << 16].cpu().numpy()
+        if dt == scl.SCL_U32:
+            exact = bool(np.array_equal(ys.view(np.uint32), oracle.map_mix32(xs.view(np.uint32))))
+        else:
+            exact = bool(np.array_equal(ys.view(np.uint32), oracle.map_poly3(xs).view(np.uint32)))
+        scl.scl_free_partition(ctx.handle, p)
+        scl.scl_free_partition(ctx.handle, q)
+        out[name] = {"gbs": 8 * n / ms / 1e6, "frac_of_hbm": 8 * n / ms / 1e6 / pk, "ms": ms,
+                     "first_65536_bit_exact": exact}
+    del x, y
     return out
 
 

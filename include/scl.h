@@ -231,10 +231,16 @@ int scl_read_partition(scl_ctx* ctx, scl_part part, void* host0, void* host1,
 int scl_map(scl_ctx* ctx, scl_part in, scl_map_kernel kernel,
             const float coef[3], void* stream, scl_part* out);
 
+/* The same map written into an existing partition of the same length and a
+ * 32-bit dtype (allocates nothing; out may equal in for an in-place map). */
+int scl_map_into(scl_ctx* ctx, scl_part in, scl_map_kernel kernel,
+                 const float coef[3], scl_part out, void* stream);
+
 /* MapCLPartition + ReduceCL over one partition, fused into one pass
  * (Sec. 3.1.3 items 2-3): y = map(x) for every element, folded by `reduce`.
  * Valid (kernel, reduce, dtype): {IDENT, MIX32} x SUM on U32/I32;
- * {IDENT, POLY3} x {SUM, SUM_MIN_MAX} on F32.  Writes *out (host) and
+ * {IDENT, POLY3} x {SUM, SUM_MIN_MAX} on F32.  (Keyed partitions: see
+ * scl_keyed_reduce / scl_keyed_reduce_hashed.)  Writes *out (host) and
  * synchronises `stream`.  Integer sums are exact; fp32 sums are fp32 within
  * 64 KB segments folded in fp64 in a fixed order, so a result is bitwise
  * reproducible and identical whether the partition runs alone or in a batch
@@ -259,6 +265,16 @@ int scl_map_reduce_async(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
 int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys,
                      void* stream, uint32_t* counts_out, float* sums_out,
                      double* sums64_out, scl_result* result);
+
+/* The keyed reduce after hashing each key into a bucket (WordCount's hash
+ * into buckets before counting, Sec. 3.2.3): pair (key, value) is counted in
+ * bucket (mix32(key) * num_keys) >> 32 (64-bit product), so every 32-bit key
+ * is valid and no pair is skipped.  Outputs and errors as scl_keyed_reduce.
+ * In a batch or server task the same reduce is kernel SCL_K_MIX32 with
+ * reduce SCL_R_KEYED_COUNT_SUM on a keyed partition. */
+int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
+                            void* stream, uint32_t* counts_out, float* sums_out,
+                            double* sums64_out, scl_result* result);
 
 /* Enqueue-only keyed reduce; outputs are DEVICE arrays (sums64 may be NULL),
  * dev_result (device, may be NULL) gets the totals and status. */

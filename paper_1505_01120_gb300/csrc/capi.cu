@@ -283,6 +283,37 @@ int scl_read_partition(scl_ctx* ctx, scl_part part, void* host0, void* host1, vo
 
 // ------------------------------------------------------------ map / reduce
 
+static int map_kind(const Partition& p, scl_map_kernel kernel, uint32_t* kind) {
+    if (p.dtype == SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "maps take a 1-array partition");
+    if (kernel == SCL_K_IDENT) *kind = K_U32_IDENT;
+    else if (kernel == SCL_K_MIX32 && p.dtype != SCL_F32) *kind = K_U32_MIX32;
+    else if (kernel == SCL_K_POLY3 && p.dtype == SCL_F32) *kind = K_F32_POLY3;
+    else return fail(SCL_E_UNSUPPORTED, "map kernel %d does not apply to dtype %d", (int)kernel,
+                     (int)p.dtype);
+    return SCL_OK;
+}
+
+static int launch_map(scl_ctx* ctx, const Partition& src, uint32_t kind, const float coef[3],
+                      void* dst, cudaStream_t st) {
+    if (!src.n) return SCL_OK;
+    static const float kDef[3] = {0.5f, -1.25f, 0.1f};
+    const float* cf = coef ? coef : kDef;
+    const int aligned = ((uintptr_t)src.d0 % 16) == 0 && ((uintptr_t)dst % 16) == 0;
+    const void* fn = map_kernel_fn((int)kind, aligned);
+    const int blk = map_kernel_block();
+    const uint64_t chunk = (uint64_t)blk * map_kernel_ipt() * 4;
+    const uint64_t want = aligned ? (src.n + chunk - 1) / chunk : (src.n + blk - 1) / blk;
+    const uint32_t grid =
+        (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->sms * 8));
+    const void* sp = src.d0;
+    uint64_t n = src.n;
+    float a = cf[0], b = cf[1], cc = cf[2];
+    void* params[] = {(void*)&sp, (void*)&dst, (void*)&n, &a, &b, &cc};
+    SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(blk), params, 0, st));
+    count_launches(1);
+    return SCL_OK;
+}
+
 int scl_map(scl_ctx* ctx, scl_part in, scl_map_kernel kernel, const float coef[3], void* stream,
             scl_part* out) {
     CTX_ENTER(ctx);
@@ -290,38 +321,30 @@ int scl_map(scl_ctx* ctx, scl_part in, scl_map_kernel kernel, const float coef[3
     const Partition* p = ctx->part(in);
     if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
     uint32_t kind;
-    if (p->dtype == SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "scl_map takes a 1-array partition");
-    if (kernel == SCL_K_IDENT) kind = K_U32_IDENT;
-    else if (kernel == SCL_K_MIX32 && p->dtype != SCL_F32) kind = K_U32_MIX32;
-    else if (kernel == SCL_K_POLY3 && p->dtype == SCL_F32) kind = K_F32_POLY3;
-    else return fail(SCL_E_UNSUPPORTED, "map kernel %d does not apply to dtype %d", (int)kernel,
-                     (int)p->dtype);
+    SCL_TRY(map_kind(*p, kernel, &kind));
     const Partition src = *p;
     Partition o;
     SCL_TRY(new_partition(ctx, src.dtype, src.n, &o));
-    if (src.n) {
-        static const float kDef[3] = {0.5f, -1.25f, 0.1f};
-        const float* cf = coef ? coef : kDef;
-        const int aligned = ((uintptr_t)src.d0 % 16) == 0;
-        const void* fn = map_kernel_fn((int)kind, aligned);
-        const int blk = map_kernel_block();
-        const uint64_t chunk = (uint64_t)blk * map_kernel_ipt() * 4;
-        uint64_t want = aligned ? (src.n + chunk - 1) / chunk : (src.n + blk - 1) / blk;
-        uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx->sms * 8));
-        void* dst = o.d0;
-        const void* sp = src.d0;
-        uint64_t n = src.n;
-        float a = cf[0], b = cf[1], cc = cf[2];
-        void* params[] = {(void*)&sp, (void*)&dst, (void*)&n, &a, &b, &cc};
-        cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(blk), params, 0, S(stream));
-        if (e != cudaSuccess) {
-            ctx->arena.release(o.block);
-            return fail(SCL_E_CUDA, "map launch failed: %s", cudaGetErrorString(e));
-        }
-        count_launches(1);
+    const int st = launch_map(ctx, src, kind, coef, o.d0, S(stream));
+    if (st != SCL_OK) {
+        ctx->arena.release(o.block);
+        return st;
     }
     *out = register_partition(ctx, o);
     return SCL_OK;
+}
+
+int scl_map_into(scl_ctx* ctx, scl_part in, scl_map_kernel kernel, const float coef[3],
+                 scl_part out, void* stream) {
+    CTX_ENTER(ctx);
+    const Partition* p = ctx->part(in);
+    const Partition* o = ctx->part(out);
+    if (!p || !o) return fail(SCL_E_INVALID, "unknown partition handle");
+    uint32_t kind;
+    SCL_TRY(map_kind(*p, kernel, &kind));
+    if (o->n != p->n || o->dtype == SCL_KV_I32_F32)
+        return fail(SCL_E_INVALID, "output partition must be a 32-bit array of the same length");
+    return launch_map(ctx, *p, kind, coef, o->d0, S(stream));
 }
 
 static int map_reduce_common(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
@@ -376,13 +399,14 @@ int scl_map_reduce_async(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, con
 }
 
 static int keyed_common(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
-                        uint32_t* counts, float* sums, double* sums64, scl_result* dres) {
+                        uint32_t* counts, float* sums, double* sums64, scl_result* dres,
+                        uint32_t kind = K_KEYED) {
     const Partition* p = ctx->part(part);
     if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
     if (p->dtype != SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "partition is not keyed");
     if (num_keys < 1 || num_keys > kMaxKeys)
         return fail(SCL_E_INVALID, "num_keys %u not in [1, %u]", num_keys, kMaxKeys);
-    return run_single(ctx, *p, K_KEYED, nullptr, num_keys, counts, sums, sums64, dres, S(stream));
+    return run_single(ctx, *p, kind, nullptr, num_keys, counts, sums, sums64, dres, S(stream));
 }
 
 int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
@@ -402,6 +426,24 @@ int scl_keyed_reduce(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* strea
     if (result) *result = *ctx->h_result;
     if (ctx->h_result->status == SCL_E_KEY_RANGE)
         return fail(SCL_E_KEY_RANGE, "a key outside [0, %u) was skipped", num_keys);
+    return SCL_OK;
+}
+
+int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                            uint32_t* counts_out, float* sums_out, double* sums64_out,
+                            scl_result* result) {
+    CTX_ENTER(ctx);
+    if (!counts_out || !sums_out) return fail(SCL_E_INVALID, "null output table");
+    uint32_t* dc = ctx->d_kout;
+    float* ds = (float*)(ctx->d_kout + kMaxKeys);
+    double* d64 = (double*)(ctx->d_kout + 2 * kMaxKeys);
+    SCL_TRY(keyed_common(ctx, part, num_keys, stream, dc, ds, d64, ctx->d_result, K_KEYED_MIX));
+    SCL_CUDA(cudaMemcpyAsync(counts_out, dc, num_keys * 4, cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaMemcpyAsync(sums_out, ds, num_keys * 4, cudaMemcpyDeviceToHost, S(stream)));
+    if (sums64_out)
+        SCL_CUDA(cudaMemcpyAsync(sums64_out, d64, num_keys * 8, cudaMemcpyDeviceToHost, S(stream)));
+    SCL_TRY(fetch_single(ctx, S(stream)));
+    if (result) *result = *ctx->h_result;
     return SCL_OK;
 }
 

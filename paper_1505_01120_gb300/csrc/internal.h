@@ -39,8 +39,11 @@ enum Kind : uint32_t {
     K_F32_IDENT = 2,   // sum / min / max of raw fp32
     K_F32_POLY3 = 3,   // sum / min / max of poly3(x)
     K_KEYED = 4,       // per-key count / sum
-    K_NUM = 5
+    K_KEYED_MIX = 5,   // per-bucket count / sum, bucket = (mix32(key) * num_keys) >> 32
+    K_NUM = 6
 };
+
+__host__ __device__ constexpr bool is_keyed(uint32_t k) { return k == K_KEYED || k == K_KEYED_MIX; }
 
 // Which kinds a compiled persistent kernel contains.
 enum Mask : uint32_t { M_U32 = 0, M_F32 = 1, M_KEYED = 2, M_ALL = 3, M_NUM = 4 };

@@ -289,8 +289,10 @@ __device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTas
 
 // ------------------------------------------------------------ keyed piece
 
+template <bool HASHED>
 __device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, uint32_t* cnt,
                                           float* sum, uint32_t& bad) {
+    if constexpr (HASHED) k = __umulhi(mix32(k), nk);   // (mix32(key) * nk) >> 32, always < nk
     if (k < nk) {           // a negative int32 key is a huge uint32: rejected here
         atomicAdd(&cnt[k], 1u);
         atomicAdd(&sum[k], __uint_as_float(v));
@@ -302,7 +304,7 @@ __device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, u
 // One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
 // shared-memory table (count, fp32 sum) and written to the outputs (single
 // piece) or to partial slot slot0 + slot.
-template <int BLOCK, int IPT>
+template <int BLOCK, int IPT, bool HASHED>
 __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
                                             uint32_t slot, uint64_t b, uint64_t e,
                                             uint32_t* tab, RedSmem& sm) {
@@ -330,10 +332,10 @@ __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& 
             for (int j = 0; j < IPT; ++j) vv[j] = ld_stream_v4(vb + off + (size_t)j * BLOCK * 16);
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                keyed_add(kv[j].x, vv[j].x, nk, cnt, sum, bad);
-                keyed_add(kv[j].y, vv[j].y, nk, cnt, sum, bad);
-                keyed_add(kv[j].z, vv[j].z, nk, cnt, sum, bad);
-                keyed_add(kv[j].w, vv[j].w, nk, cnt, sum, bad);
+                keyed_add<HASHED>(kv[j].x, vv[j].x, nk, cnt, sum, bad);
+                keyed_add<HASHED>(kv[j].y, vv[j].y, nk, cnt, sum, bad);
+                keyed_add<HASHED>(kv[j].z, vv[j].z, nk, cnt, sum, bad);
+                keyed_add<HASHED>(kv[j].w, vv[j].w, nk, cnt, sum, bad);
             }
         }
     }
@@ -344,8 +346,8 @@ __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& 
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (g + q < e)
-                    keyed_add(ld_stream_b32(kb + (g + q) * 4), ld_stream_b32(vb + (g + q) * 4), nk,
-                              cnt, sum, bad);
+                    keyed_add<HASHED>(ld_stream_b32(kb + (g + q) * 4),
+                                      ld_stream_b32(vb + (g + q) * 4), nk, cnt, sum, bad);
         }
     }
     const int any_bad = __syncthreads_or((int)bad);
@@ -389,18 +391,24 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ Ke
     if constexpr (mask_has_keyed(MASK)) {
         uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
         if (a.tasks == nullptr) {
-            if (a.single.kind == K_KEYED && blockIdx.x < a.nkeyed_ctas) {
+            if (is_keyed(a.single.kind) && blockIdx.x < a.nkeyed_ctas) {
                 const uint32_t G = a.nkeyed_ctas;
-                keyed_piece<BLOCK, IPT>(a, a.single, 0u, blockIdx.x,
-                                        keyed_single_bound(a.single.n, blockIdx.x, G),
-                                        keyed_single_bound(a.single.n, blockIdx.x + 1, G), tab, sm);
+                const uint64_t b = keyed_single_bound(a.single.n, blockIdx.x, G);
+                const uint64_t e = keyed_single_bound(a.single.n, blockIdx.x + 1, G);
+                if (a.single.kind == K_KEYED_MIX)
+                    keyed_piece<BLOCK, IPT, true>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
+                else
+                    keyed_piece<BLOCK, IPT, false>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
             }
         } else {
             const uint32_t p0 = a.kp_first[blockIdx.x], p1 = a.kp_first[blockIdx.x + 1];
             for (uint32_t p = p0; p < p1; ++p) {
                 const KPiece kp = a.kpieces[p];
                 const DevTask t = a.tasks[kp.task];
-                keyed_piece<BLOCK, IPT>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                if (t.kind == K_KEYED_MIX)
+                    keyed_piece<BLOCK, IPT, true>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                else
+                    keyed_piece<BLOCK, IPT, false>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
             }
         }
     }

@@ -176,6 +176,10 @@ int resolve_kind(scl_dtype dt, int kernel, int reduce, uint32_t* kind) {
                 *kind = K_KEYED;
                 return SCL_OK;
             }
+            if (reduce == SCL_R_KEYED_COUNT_SUM && kernel == SCL_K_MIX32) {
+                *kind = K_KEYED_MIX;
+                return SCL_OK;
+            }
             break;
         default:
             return fail(SCL_E_INVALID, "unknown dtype %d", (int)dt);
@@ -332,7 +336,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     t.sums_out = sums;
     t.sums64_out = sums64;
     uint32_t grid;
-    if (kind == K_KEYED) {
+    if (is_keyed(kind)) {
         const uint32_t G = keyed_single_pieces(p.n, gmax);
         t.nseg = G;
         a.nkeyed_ctas = G;
@@ -353,7 +357,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     a.task_flags = c->single.flags;
     a.hdr = c->single.hdr;
     SCL_TRY(launch_entry(e, grid, a, st));
-    if (kind == K_KEYED && t.nseg > 1) {
+    if (is_keyed(kind) && t.nseg > 1) {
         const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;
         void* params[] = {&a};
         SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(nkb, 1), dim3(kFoldBlock), params, 0, st));
@@ -374,7 +378,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
                             (unsigned long long)in[i].part);
         SCL_TRY(resolve_kind(p->dtype, in[i].kernel, in[i].reduce, &kind[i]));
         uint32_t nk = 0;
-        if (kind[i] == K_KEYED) {
+        if (is_keyed(kind[i])) {
             nk = in[i].num_keys;
             if (nk < 1 || nk > kMaxKeys)
                 return fail(SCL_E_INVALID, "task %u: num_keys %u not in [1, %u]", i, nk, kMaxKeys);
@@ -388,7 +392,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
         t.sums64_out = in[i].sums64_out;
         has_u32 |= mask_of_kind(kind[i]) == M_U32;
         has_f32 |= mask_of_kind(kind[i]) == M_F32;
-        has_keyed |= kind[i] == K_KEYED;
+        has_keyed |= is_keyed(kind[i]);
     }
     const int ntypes = (int)has_u32 + (int)has_f32 + (int)has_keyed;
     P->mask = ntypes > 1 ? M_ALL : has_keyed ? M_KEYED : has_f32 ? M_F32 : M_U32;
@@ -405,7 +409,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     uint64_t W = 0;   // keyed cost
     for (uint32_t i = 0; i < nt; ++i) {
         DevTask& t = P->tasks[i];
-        if (kind[i] == K_KEYED) {
+        if (is_keyed(kind[i])) {
             W += t.n + kKeyedTaskOverhead;
             continue;
         }
@@ -438,7 +442,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
         std::vector<uint32_t> cta_of_piece;
         uint64_t A = 0;
         for (uint32_t i = 0; i < nt; ++i) {
-            if (kind[i] != K_KEYED) continue;
+            if (!is_keyed(kind[i])) continue;
             DevTask& t = P->tasks[i];
             const uint64_t cost = t.n + kKeyedTaskOverhead, B = A + cost;
             uint32_t c0 = (uint32_t)((unsigned __int128)A * Gk / W);

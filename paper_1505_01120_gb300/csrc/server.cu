@@ -346,7 +346,7 @@ static int submit_common(scl_ctx* ctx, SrvTask&& t, const Partition& p, uint64_t
     SCL_TRY(srv_of(ctx, &s));
     uint32_t kind;
     SCL_TRY(resolve_kind(p.dtype, t.task.kernel, t.task.reduce, &kind));
-    if (kind == K_KEYED) {
+    if (is_keyed(kind)) {
         if (t.task.num_keys < 1 || t.task.num_keys > kMaxKeys)
             return fail(SCL_E_INVALID, "num_keys %u not in [1, %u]", t.task.num_keys, kMaxKeys);
         if (!t.task.counts_out || !t.task.sums_out)

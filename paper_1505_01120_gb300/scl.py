@@ -141,12 +141,15 @@ _SIGS = {
                             _PP, _PP], ctypes.c_int),
     "scl_read_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
     "scl_map": ([_P, _u64, ctypes.c_int, _P, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_map_into": ([_P, _u64, ctypes.c_int, _P, _u64, _P], ctypes.c_int),
     "scl_map_reduce": ([_P, _u64, ctypes.c_int, _P, ctypes.c_int, _P,
                         ctypes.POINTER(scl_result)], ctypes.c_int),
     "scl_map_reduce_async": ([_P, _u64, ctypes.c_int, _P, ctypes.c_int, _P, _P], ctypes.c_int),
     "scl_keyed_reduce": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
                          ctypes.c_int),
     "scl_keyed_reduce_async": ([_P, _u64, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "scl_keyed_reduce_hashed": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
+                                ctypes.c_int),
     "scl_reduce_arrays": ([_P, _P, _u32, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_reduce_arrays_into": ([_P, _P, _u32, _u64, _P], ctypes.c_int),
     "scl_vector_add": ([_P, _u64, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
@@ -299,6 +302,11 @@ def scl_map(ctx: int, part: int, kernel: int, coef=None, stream: int = 0) -> int
     return out.value
 
 
+def scl_map_into(ctx: int, part: int, kernel: int, out: int, coef=None, stream: int = 0) -> None:
+    c = _coef(coef)
+    _check(lib.scl_map_into(ctx, part, kernel, _ptr(c), out, stream))
+
+
 def scl_map_reduce(ctx: int, part: int, kernel: int, reduce: int, coef=None,
                    stream: int = 0) -> scl_result:
     c = _coef(coef)
@@ -329,6 +337,18 @@ def scl_keyed_reduce(ctx: int, part: int, num_keys: int = 4096, stream: int = 0,
         err.tables = (counts, sums, s64, r)
         raise err
     _check(st)
+    return counts, sums, s64, r
+
+
+def scl_keyed_reduce_hashed(ctx: int, part: int, num_keys: int = 4096, stream: int = 0,
+                            want_f64: bool = True):
+    """Keyed reduce with keys hashed into buckets: (counts, sums, sums64, result)."""
+    counts = np.empty(num_keys, np.uint32)
+    sums = np.empty(num_keys, np.float32)
+    s64 = np.empty(num_keys, np.float64) if want_f64 else None
+    r = scl_result()
+    _check(lib.scl_keyed_reduce_hashed(ctx, part, num_keys, stream, _ptr(counts), _ptr(sums),
+                                       _ptr(s64), ctypes.byref(r)))
     return counts, sums, s64, r
 
 

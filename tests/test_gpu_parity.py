@@ -196,6 +196,27 @@ def test_map_materialised_bit_exact(env):
     assert np.array_equal(out, oracle.map_mix32(a[1:]))
 
 
+def test_map_into_existing_and_in_place(env):
+    c, scl, st, torch = env
+    rng = np.random.default_rng(112)
+    x = rng.standard_normal(70_003, dtype=np.float32)
+    p = scl.scl_load_partition(c.handle, x, scl.SCL_F32, stream=st)
+    q = scl.scl_load_partition(c.handle, np.zeros_like(x), scl.SCL_F32, stream=st)
+    free0 = scl.scl_arena_stats(c.handle)[0]
+    scl.scl_map_into(c.handle, p, scl.SCL_K_POLY3, q, stream=st)
+    assert scl.scl_arena_stats(c.handle)[0] == free0
+    y = np.empty_like(x)
+    scl.scl_read_partition(c.handle, q, y, stream=st)
+    assert np.array_equal(y.view(np.uint32), oracle.map_poly3(x).view(np.uint32))
+    scl.scl_map_into(c.handle, p, scl.SCL_K_POLY3, p, stream=st)      # in place
+    scl.scl_read_partition(c.handle, p, y, stream=st)
+    assert np.array_equal(y.view(np.uint32), oracle.map_poly3(x).view(np.uint32))
+    r = scl.scl_load_partition(c.handle, np.zeros(5, np.float32), scl.SCL_F32, stream=st)
+    with pytest.raises(scl.SclError) as e:
+        scl.scl_map_into(c.handle, p, scl.SCL_K_POLY3, r, stream=st)
+    assert e.value.status == scl.SCL_E_INVALID
+
+
 def test_async_result_in_device_memory(env):
     c, scl, st, torch = env
     a = np.random.default_rng(111).integers(0, 1 << 32, size=123_457, dtype=np.uint32)
