@@ -573,6 +573,48 @@ def batch_config(torch, scl, ctx, stream) -> dict:
             "batched_equals_per_launch_f32": same_f32}
 
 
+def run_ncu_case(args):
+    """Small profiler cases of the other families (same kernels and sizes as
+    the configs, a few launches, a 3 GiB arena): 'keyed' = 16 x 16 Mi pairs
+    keyed count+sum; 'tree' = vector-add ReduceCL of 64 x 4 Mi fp32 arrays."""
+    import torch
+    from paper_1505_01120_gb300 import scl
+    from paper_1505_01120_gb300.context import Context
+    torch.cuda.set_device(0)
+    ctx = Context(3 << 30)
+    stream = torch.cuda.Stream()
+    st = stream.cuda_stream
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    if args.ncu_case == "keyed":
+        m = 1 << 24
+        keys = torch.randint(0, 4096, (16 * m,), dtype=torch.int32, device="cuda", generator=g)
+        vals = torch.rand(16 * m, device="cuda", generator=g)
+        outs = torch.zeros((16, 4096 * 4), dtype=torch.int32, device="cuda")
+        tasks = []
+        for i in range(16):
+            q = scl.scl_wrap_device(ctx.handle, keys.data_ptr() + i * m * 4,
+                                    vals.data_ptr() + i * m * 4, scl.SCL_KV_I32_F32, m)
+            base = outs[i].data_ptr()
+            tasks.append(dict(part=q, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                              num_keys=4096, counts_out=base, sums_out=base + 16384,
+                              sums64_out=base + 32768))
+        b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
+        fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
+    else:
+        k, n = 64, 1 << 22
+        x = torch.randn(k * n, device="cuda", generator=g)
+        parts = [scl.scl_wrap_device(ctx.handle, x.data_ptr() + j * n * 4, None, scl.SCL_F32, n)
+                 for j in range(k)]
+        out = scl.scl_reduce_arrays(ctx.handle, parts, stream=st)
+        fn = lambda: scl.scl_reduce_arrays_into(ctx.handle, parts, out, stream=st)  # noqa: E731
+    for _ in range(args.warmup + args.steps):
+        fn()
+    torch.cuda.synchronize()
+    log("ncu case %s done" % args.ncu_case)
+    ctx.close()
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1505_01120_gb300 import scl
@@ -775,8 +817,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--full", action="store_true", help="longer serving runs")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="profiler case: headline kernel only, small arena, no JSON line")
+    ap.add_argument("--ncu-case", nargs="?", const="headline", default=None,
+                    choices=["headline", "keyed", "tree"],
+                    help="profiler case: one workload's kernel only, small arena, no JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -784,6 +827,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.ncu_case in ("keyed", "tree"):
+        run_ncu_case(args)
     else:
         run_ours(args, rank, world)
 
