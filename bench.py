@@ -320,6 +320,7 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
 
     out["keyed_hashed_count_sum_16x16777216"] = keyed_hashed_config(torch, scl, ctx, stream, pk)
     out["map_materialised_268435456"] = map_config(torch, scl, ctx, stream, pk)
+    out["keyed_large_1048576_keys"] = keyed_large_config(torch, scl, ctx, stream, pk)
     out["vector_add_reduce_64x4194304"] = vector_add_config(torch, scl, ctx, stream, pk)
     out["batch_10000"] = batch_config(torch, scl, ctx, stream)
     out["serve"] = serve_config(torch, scl, ctx, stream, full)
@@ -435,6 +436,32 @@ def keyed_hashed_config(torch, scl, ctx, stream, pk: float) -> dict:
             "partition0_counts_exact": bool(np.array_equal(o0[:4096].view(np.uint32), ocnt)),
             "partition0_max_rel_err": float(np.max(np.abs(o0[8192:].view(np.float64) - osum)
                                                    / np.abs(osum)))}
+
+
+def keyed_large_config(torch, scl, ctx, stream, pk: float) -> dict:
+    """Keyed count+sum over 2^20 keys, 64 Mi pairs: uniform keys, and Zipf(1.2)
+    keys numbered by frequency (hot ids in the shared table)."""
+    import oracle
+    st = stream.cuda_stream
+    nk, n = 1 << 20, 1 << 26
+    out = {}
+    for name in ("uniform", "zipf"):
+        rng = np.random.default_rng(10)
+        keys = synth.keys_i32(n, rng, nk) if name == "uniform" else synth.zipf_keys_i32(n, rng, nk)
+        vals = synth.unit_f32(n, rng)
+        p = scl.scl_load_partition_kv(ctx.handle, keys, vals, stream=st)
+        dc = torch.empty(nk, dtype=torch.int32, device="cuda")
+        ds = torch.empty(nk, dtype=torch.float32, device="cuda")
+        d64 = torch.empty(nk, dtype=torch.float64, device="cuda")
+        dr = torch.empty(48, dtype=torch.uint8, device="cuda")
+        ms = time_device(torch, stream, lambda: scl.scl_keyed_reduce_large_async(
+            ctx.handle, p, nk, dc, ds, d64, dr, stream=st), 10)
+        ocnt, _, _ = oracle.keyed_count_sum(keys, vals, nk)
+        exact = bool(np.array_equal(dc.cpu().numpy().view(np.uint32), ocnt))
+        scl.scl_free_partition(ctx.handle, p)
+        out[name] = {"gbs": 8 * n / ms / 1e6, "frac_of_hbm": 8 * n / ms / 1e6 / pk, "ms": ms,
+                     "pairs_per_s": n / ms * 1e3, "counts_exact": exact}
+    return out
 
 
 def map_config(torch, scl, ctx, stream, pk: float) -> dict:

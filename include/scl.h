@@ -276,6 +276,31 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
                             void* stream, uint32_t* counts_out, float* sums_out,
                             double* sums64_out, scl_result* result);
 
+/* Largest key space of scl_keyed_reduce_large (2^24 keys). */
+#define SCL_MAX_LARGE_KEYS 16777216u
+
+/* The keyed reduce for key spaces larger than 4096 (a WordCount-size
+ * vocabulary, Sec. 3.2.3): keys below 4096 -- the frequent ids when words
+ * are numbered by frequency -- are counted in a per-block shared-memory table
+ * flushed every 131,072 pairs; every other key goes straight to global
+ * atomics (uint32 count, fp64 sum).  num_keys in [1, SCL_MAX_LARGE_KEYS].
+ * HOST outputs of num_keys entries; sums_out is the fp64 sum rounded to fp32.
+ * Counts are exact; sums agree with an fp64 fold to about 1e-7 (atomic order
+ * varies between runs).  Uses temporary device tables from the arena
+ * (16 B per key).  Returns SCL_E_KEY_RANGE after writing the valid pairs'
+ * tables if a key was outside [0, num_keys). */
+int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                           uint32_t* counts_out, float* sums_out, double* sums64_out,
+                           scl_result* result);
+
+/* Enqueue-only form on DEVICE tables the caller owns: counts_dev (uint32),
+ * sums_dev (float) and sums64_dev (double, required: it is the accumulator),
+ * num_keys entries each, and dev_result (one scl_result).  All are zeroed or
+ * overwritten on `stream` before use. */
+int scl_keyed_reduce_large_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,
+                                 void* stream, uint32_t* counts_dev, float* sums_dev,
+                                 double* sums64_dev, scl_result* dev_result);
+
 /* Enqueue-only keyed reduce; outputs are DEVICE arrays (sums64 may be NULL),
  * dev_result (device, may be NULL) gets the totals and status. */
 int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,

@@ -447,6 +447,106 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys, void
     return SCL_OK;
 }
 
+static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uint32_t* counts,
+                              float* sums, double* sums64, scl_result* res, cudaStream_t st) {
+    if (!ctx->d_large) {
+        ctx->d_large = (uint32_t*)ctx->arena.alloc(kAlign);
+        if (!ctx->d_large) return fail(SCL_E_NOMEM, "arena: no room for scratch");
+        SCL_CUDA(cudaMemset(ctx->d_large, 0, kAlign));
+        SCL_CUDA(cudaDeviceSynchronize());
+    }
+    LargeKeyedArgs a;
+    memset(&a, 0, sizeof a);
+    a.keys = static_cast<const char*>(p.d0);
+    a.vals = static_cast<const char*>(p.d1);
+    a.n = p.n;
+    a.num_keys = nk;
+    a.aligned = ((uintptr_t)p.d0 % 16) == 0 && ((uintptr_t)p.d1 % 16) == 0;
+    a.counts = counts;
+    a.sums64 = sums64;
+    a.sums32 = sums;
+    a.result = res;
+    a.ticket = ctx->d_large;       // reset to zero by the finishing pass
+    a.bad = ctx->d_large + 1;
+    SCL_CUDA(cudaMemsetAsync(counts, 0, (size_t)nk * 4, st));
+    SCL_CUDA(cudaMemsetAsync(sums64, 0, (size_t)nk * 8, st));
+    SCL_CUDA(cudaMemsetAsync(res, 0, sizeof(scl_result), st));
+    SCL_CUDA(cudaMemsetAsync(a.bad, 0, 4, st));
+    void* params[] = {&a};
+    if (p.n) {
+        const void* fn = large_keyed_kernel_fn(a.aligned);
+        int nb = 0;
+        SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0));
+        const uint64_t pieces = (p.n + kLargePiece - 1) / kLargePiece;
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(
+            1, std::min<uint64_t>(pieces, (uint64_t)ctx->sms * std::max(nb, 1)));
+        SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(256), params, 0, st));
+        count_launches(1);
+    }
+    const uint32_t fgrid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(((uint64_t)nk + 255) / 256, (uint64_t)ctx->sms * 8));
+    SCL_CUDA(cudaLaunchKernel(large_keyed_finish_fn(), dim3(fgrid), dim3(256), params, 0, st));
+    count_launches(1);
+    return SCL_OK;
+}
+
+static int large_part(scl_ctx* ctx, scl_part part, uint32_t nk, const Partition** out) {
+    const Partition* p = ctx->part(part);
+    if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
+    if (p->dtype != SCL_KV_I32_F32) return fail(SCL_E_UNSUPPORTED, "partition is not keyed");
+    if (nk < 1 || nk > kMaxLargeKeys)
+        return fail(SCL_E_INVALID, "num_keys %u not in [1, %u]", nk, kMaxLargeKeys);
+    *out = p;
+    return SCL_OK;
+}
+
+int scl_keyed_reduce_large_async(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                                 uint32_t* counts_dev, float* sums_dev, double* sums64_dev,
+                                 scl_result* dev_result) {
+    CTX_ENTER(ctx);
+    const Partition* p = nullptr;
+    SCL_TRY(large_part(ctx, part, num_keys, &p));
+    if (!counts_dev || !sums_dev || !sums64_dev || !dev_result)
+        return fail(SCL_E_INVALID, "all device tables and the result are required");
+    return launch_large_keyed(ctx, *p, num_keys, counts_dev, sums_dev, sums64_dev, dev_result,
+                              S(stream));
+}
+
+int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
+                           uint32_t* counts_out, float* sums_out, double* sums64_out,
+                           scl_result* result) {
+    CTX_ENTER(ctx);
+    const Partition* p = nullptr;
+    SCL_TRY(large_part(ctx, part, num_keys, &p));
+    if (!counts_out || !sums_out) return fail(SCL_E_INVALID, "null output table");
+    const size_t nk = num_keys;
+    char* buf = (char*)ctx->arena.alloc(nk * 16 + kAlign);
+    if (!buf) return fail(SCL_E_NOMEM, "arena: no room for %u-key tables", num_keys);
+    double* d64 = (double*)buf;
+    uint32_t* dc = (uint32_t*)(buf + nk * 8);
+    float* ds = (float*)(buf + nk * 12);
+    scl_result* dr = (scl_result*)(buf + align_up(nk * 16));
+    int st = launch_large_keyed(ctx, *p, num_keys, dc, ds, d64, dr, S(stream));
+    if (st == SCL_OK) {
+        cudaStream_t s = S(stream);
+        if (cudaMemcpyAsync(counts_out, dc, nk * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(sums_out, ds, nk * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            (sums64_out &&
+             cudaMemcpyAsync(sums64_out, d64, nk * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+            cudaMemcpyAsync(ctx->h_result, dr, sizeof(scl_result), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = fail(SCL_E_CUDA, "large keyed reduce: copy back failed");
+    }
+    cudaStreamSynchronize(S(stream));
+    ctx->arena.release(buf);
+    if (st != SCL_OK) return st;
+    if (result) *result = *ctx->h_result;
+    if (ctx->h_result->status == SCL_E_KEY_RANGE)
+        return fail(SCL_E_KEY_RANGE, "a key outside [0, %u) was skipped", num_keys);
+    return SCL_OK;
+}
+
 int scl_keyed_reduce_async(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
                            uint32_t* counts_out, float* sums_out, double* sums64_out,
                            scl_result* dev_result) {

@@ -152,6 +152,27 @@ struct TreeArgs {
     uint32_t pad;
 };
 
+// Keyed reduce over key spaces larger than the shared table: keys below
+// kMaxKeys are accumulated in a per-CTA shared-memory table (the hot ids of a
+// frequency-ordered dictionary) and flushed every kLargePiece pairs; the rest
+// go straight to global count / fp64 sum atomics.
+constexpr uint32_t kMaxLargeKeys = 1u << 24;
+constexpr uint64_t kLargePiece = 131072;
+
+struct LargeKeyedArgs {
+    const char* keys;
+    const char* vals;
+    uint64_t n;
+    uint32_t num_keys;
+    uint32_t aligned;
+    uint32_t* counts;         // [num_keys], zeroed before the launch
+    double* sums64;           // [num_keys], zeroed before the launch
+    float* sums32;            // [num_keys] written by the finishing pass
+    scl_result* result;       // zeroed before the launch
+    uint32_t* ticket;         // zero between launches (finishing pass)
+    uint32_t* bad;            // zeroed before the launch
+};
+
 // Host-side launch entry of one compiled persistent-kernel instantiation.
 struct KernelEntry {
     int mask, block, ipt;              // block = threads that touch data (consumers)
@@ -172,5 +193,7 @@ extern const void* map_kernel_fn(int kind, int aligned);
 extern int map_kernel_block();
 extern int map_kernel_ipt();
 extern const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k);
+extern const void* large_keyed_kernel_fn(int aligned);
+extern const void* large_keyed_finish_fn();
 
 }  // namespace scl

@@ -39,4 +39,10 @@ const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k) {
 #undef SCL_TREE
 }
 
+const void* large_keyed_kernel_fn(int aligned) {
+    return aligned ? (const void*)&dev::k_keyed_large<true> : (const void*)&dev::k_keyed_large<false>;
+}
+
+const void* large_keyed_finish_fn() { return (const void*)&dev::k_keyed_large_finish<256>; }
+
 }  // namespace scl

@@ -666,6 +666,110 @@ __global__ void __launch_bounds__(256) k_tree_add(const __grid_constant__ TreeAr
     }
 }
 
+// ------------------------------------------------- large key spaces
+
+__device__ __forceinline__ void large_add(uint32_t k, uint32_t vbits, const LargeKeyedArgs& a,
+                                          uint32_t* hc, float* hs, uint32_t& bad) {
+    const float v = __uint_as_float(vbits);
+    if (k >= a.num_keys) {
+        bad = 1u;
+    } else if (k < kMaxKeys) {
+        atomicAdd(&hc[k], 1u);
+        atomicAdd(&hs[k], v);
+    } else {
+        atomicAdd(&a.counts[k], 1u);
+        atomicAdd(&a.sums64[k], (double)v);
+    }
+}
+
+// Grid-stride over pieces of kLargePiece pairs; each piece zeroes the shared
+// hot table, accumulates, and flushes its non-zero entries to global memory.
+template <bool ALIGNED>
+__global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ LargeKeyedArgs a) {
+    __shared__ uint32_t hc[kMaxKeys];
+    __shared__ float hs[kMaxKeys];
+    const uint32_t hot = min(a.num_keys, kMaxKeys);
+    const uint64_t npieces = (a.n + kLargePiece - 1) / kLargePiece;
+    uint32_t bad = 0;
+    for (uint64_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
+        for (uint32_t i = threadIdx.x; i < hot; i += blockDim.x) {
+            hc[i] = 0u;
+            hs[i] = 0.f;
+        }
+        __syncthreads();
+        const uint64_t b = pc * kLargePiece;
+        const uint64_t e = min(b + kLargePiece, a.n);
+        uint64_t i = b;
+        if constexpr (ALIGNED) {
+            constexpr uint32_t CH = 256 * 4 * 4;
+            for (; i + CH <= e; i += CH) {
+                uint4 kv[4], vv[4];
+                const uint64_t off = (i + (uint64_t)threadIdx.x * 4) * 4;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) kv[j] = ld_stream_v4(a.keys + off + (size_t)j * 4096);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) vv[j] = ld_stream_v4(a.vals + off + (size_t)j * 4096);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    large_add(kv[j].x, vv[j].x, a, hc, hs, bad);
+                    large_add(kv[j].y, vv[j].y, a, hc, hs, bad);
+                    large_add(kv[j].z, vv[j].z, a, hc, hs, bad);
+                    large_add(kv[j].w, vv[j].w, a, hc, hs, bad);
+                }
+            }
+        }
+        for (uint64_t g = i + threadIdx.x; g < e; g += blockDim.x)
+            large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, hc, hs, bad);
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < hot; k += blockDim.x) {
+            const uint32_t c = hc[k];
+            if (c) {
+                atomicAdd(&a.counts[k], c);
+                atomicAdd(&a.sums64[k], (double)hs[k]);
+            }
+        }
+        __syncthreads();   // the table is zeroed again by the next piece
+    }
+    if (bad) atomicOr(a.bad, 1u);
+}
+
+// Finishing pass: fp32 sums, totals (count exact, value sum fp64) and status.
+// The last CTA writes f32_sum and resets the ticket.
+template <int FB>
+__global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant__ LargeKeyedArgs a) {
+    static_assert(FB == 256, "finish block");
+    __shared__ RedSmem sm;
+    unsigned long long c = 0;
+    double s = 0.0;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.num_keys;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const double v = a.sums64[k];
+        a.sums32[k] = (float)v;
+        c += a.counts[k];
+        s += v;
+    }
+    float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
+    block_reduce_f<256>(s, d0, d1, sm);
+    c = block_sum_u64<256>(c, sm);
+    if (threadIdx.x == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.result->u64_sum), c);
+        atomicAdd(&a.result->f64_sum, s);
+        __threadfence();
+        if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
+            __threadfence();
+            scl_result* r = a.result;
+            const double tot = __ldcg(&r->f64_sum);
+            r->f32_sum = (float)tot;
+            r->f32_min = CUDART_INF_F;
+            r->f32_max = -CUDART_INF_F;
+            r->status = __ldcg(a.bad) ? SCL_E_KEY_RANGE : SCL_OK;
+            r->n = a.n;
+            r->kind = K_KEYED;
+            *a.ticket = 0u;
+        }
+    }
+}
+
 }  // namespace dev
 }  // namespace scl
 

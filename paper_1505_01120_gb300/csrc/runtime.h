@@ -184,6 +184,7 @@ struct Ctx {
     scl_result* d_result = nullptr;        // single-call result slot
     scl_result* h_result = nullptr;        // pinned
     uint32_t* d_kout = nullptr;            // single-call keyed outputs (counts|sums|sums64)
+    uint32_t* d_large = nullptr;           // large-key reduce: ticket, bad-key flag
     std::string tune_path;
     std::unique_ptr<Server> server;
 

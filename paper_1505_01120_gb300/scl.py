@@ -37,6 +37,7 @@ SCL_K_IDENT, SCL_K_MIX32, SCL_K_POLY3 = 0, 1, 2
 SCL_R_NONE, SCL_R_SUM, SCL_R_SUM_MIN_MAX, SCL_R_KEYED_COUNT_SUM = 0, 1, 2, 3
 SCL_NOALLOC_MAX_ELEMENTS = 67_108_864
 SCL_MAX_REDUCE_ARRAYS = 1024
+SCL_MAX_LARGE_KEYS = 1 << 24
 
 
 class scl_config(ctypes.Structure):
@@ -148,6 +149,9 @@ _SIGS = {
     "scl_keyed_reduce": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
                          ctypes.c_int),
     "scl_keyed_reduce_async": ([_P, _u64, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "scl_keyed_reduce_large": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
+                               ctypes.c_int),
+    "scl_keyed_reduce_large_async": ([_P, _u64, _u32, _P, _P, _P, _P, _P], ctypes.c_int),
     "scl_keyed_reduce_hashed": ([_P, _u64, _u32, _P, _P, _P, _P, ctypes.POINTER(scl_result)],
                                 ctypes.c_int),
     "scl_reduce_arrays": ([_P, _P, _u32, _P, ctypes.POINTER(_u64)], ctypes.c_int),
@@ -350,6 +354,30 @@ def scl_keyed_reduce_hashed(ctx: int, part: int, num_keys: int = 4096, stream: i
     _check(lib.scl_keyed_reduce_hashed(ctx, part, num_keys, stream, _ptr(counts), _ptr(sums),
                                        _ptr(s64), ctypes.byref(r)))
     return counts, sums, s64, r
+
+
+def scl_keyed_reduce_large(ctx: int, part: int, num_keys: int, stream: int = 0,
+                           want_f64: bool = True):
+    """Keyed reduce for key spaces up to 2^24: (counts, sums, sums64, result).
+    Raises SclError(SCL_E_KEY_RANGE) with .tables after a skipped key."""
+    counts = np.empty(num_keys, np.uint32)
+    sums = np.empty(num_keys, np.float32)
+    s64 = np.empty(num_keys, np.float64) if want_f64 else None
+    r = scl_result()
+    st = lib.scl_keyed_reduce_large(ctx, part, num_keys, stream, _ptr(counts), _ptr(sums),
+                                    _ptr(s64), ctypes.byref(r))
+    if st == SCL_E_KEY_RANGE:
+        err = SclError(st, lib.scl_last_error().decode())
+        err.tables = (counts, sums, s64, r)
+        raise err
+    _check(st)
+    return counts, sums, s64, r
+
+
+def scl_keyed_reduce_large_async(ctx: int, part: int, num_keys: int, counts_dev, sums_dev,
+                                 sums64_dev, result_dev, stream: int = 0) -> None:
+    _check(lib.scl_keyed_reduce_large_async(ctx, part, num_keys, stream, _ptr(counts_dev),
+                                            _ptr(sums_dev), _ptr(sums64_dev), _ptr(result_dev)))
 
 
 def scl_keyed_reduce_async(ctx: int, part: int, num_keys: int, counts_dev, sums_dev,

@@ -46,6 +46,13 @@ def keys_i32(n: int, rng: np.random.Generator, num_keys: int = NUM_KEYS) -> np.n
     return rng.integers(0, num_keys, size=n, dtype=np.int32)
 
 
+def zipf_keys_i32(n: int, rng: np.random.Generator, num_keys: int, s: float = 1.2) -> np.ndarray:
+    """Keys with Zipf-like frequencies: numpy's zipf(s) ranks minus one, wrapped
+    into [0, num_keys), so id 0 is the most frequent (a dictionary numbered by
+    frequency, as WordCount's vocabulary would be)."""
+    return ((rng.zipf(s, size=n) - 1) % num_keys).astype(np.int32)
+
+
 def unit_f32(n: int, rng: np.random.Generator, out=None) -> np.ndarray:
     if out is not None:
         rng.random(size=n, dtype=np.float32, out=out)
