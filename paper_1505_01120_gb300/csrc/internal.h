@@ -107,6 +107,7 @@ struct KernelArgs {
     uint32_t nkeyed_ctas;       // single-task keyed mode: number of pieces
     uint32_t nfold;             // entries of fold_tasks (batch mode)
     uint32_t pad;
+    uint32_t* err_out;          // if set, the last CTA to exit copies H_ERROR here
     DevTask single;
 };
 

@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(CB + 32) k_stream_tma(const __grid_constant__ 
         if (done == gridDim.x - 1) {
             atomicExch(&a.hdr[H_QUEUE], 0u);
             atomicExch(&a.hdr[H_EXIT], 0u);
+            if (a.err_out) *a.err_out = atomicOr(&a.hdr[H_ERROR], 0u);
         }
     }
 }

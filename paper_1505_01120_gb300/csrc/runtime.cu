@@ -491,8 +491,13 @@ static T* carve(char* base, size_t* off, size_t count) {
     return p;
 }
 
-int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, KernelArgs* args) {
+int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, KernelArgs* args,
+                const ExternalScratch* ext) {
     const size_t nt = p.tasks.size();
+    if (ext && nt > ext->task_cap)
+        return fail(SCL_E_INVALID, "batch of %zu tasks exceeds the scratch capacity %zu", nt,
+                    ext->task_cap);
+    const size_t own = ext ? 0 : nt;   // results / counters carried in the block
     // sizes (offsets relative to the block)
     size_t off = 0;
     char* nil = nullptr;
@@ -502,11 +507,11 @@ int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, Kernel
     auto o_kp = off; carve<KPiece>(nil, &off, p.kpieces.size());
     auto o_fold = off; carve<uint32_t>(nil, &off, p.fold_tasks.size());
     const size_t plan_bytes = off;
-    auto o_res = off; carve<scl_result>(nil, &off, nt);
+    auto o_res = off; carve<scl_result>(nil, &off, own);
     const size_t zero_off = off;
-    auto o_hdr = off; carve<uint32_t>(nil, &off, H_WORDS);
-    auto o_tk = off; carve<uint32_t>(nil, &off, nt);
-    auto o_fl = off; carve<uint32_t>(nil, &off, nt);
+    auto o_hdr = off; carve<uint32_t>(nil, &off, ext ? 0 : H_WORDS);
+    auto o_tk = off; carve<uint32_t>(nil, &off, own);
+    auto o_fl = off; carve<uint32_t>(nil, &off, own);
     const size_t zero_bytes = off - zero_off;
     auto o_sp = off; carve<StreamPartial>(nil, &off, p.sslots);
     auto o_fp = off; carve<StreamPartial>(nil, &off, p.fold_tasks.size() * (kMaxKeys / kFoldBlock));
@@ -522,10 +527,10 @@ int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, Kernel
     img->kp_first = (uint32_t*)(b + o_kpf);
     img->kpieces = (KPiece*)(b + o_kp);
     img->fold_tasks = (uint32_t*)(b + o_fold);
-    img->results = (scl_result*)(b + o_res);
-    img->hdr = (uint32_t*)(b + o_hdr);
-    img->tickets = (uint32_t*)(b + o_tk);
-    img->flags = (uint32_t*)(b + o_fl);
+    img->results = ext ? ext->results : (scl_result*)(b + o_res);
+    img->hdr = ext ? ext->hdr : (uint32_t*)(b + o_hdr);
+    img->tickets = ext ? ext->tickets : (uint32_t*)(b + o_tk);
+    img->flags = ext ? ext->flags : (uint32_t*)(b + o_fl);
     img->spart = (StreamPartial*)(b + o_sp);
     img->fpart = (StreamPartial*)(b + o_fp);
     img->kpart = (uint32_t*)(b + o_kt);
@@ -556,6 +561,7 @@ int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, Kernel
     args->hdr = img->hdr;
     args->nseg_stream = p.nseg_stream;
     args->nfold = (uint32_t)p.fold_tasks.size();
+    args->err_out = ext ? ext->err_out : nullptr;
     return SCL_OK;
 }
 

@@ -153,9 +153,24 @@ struct PlanImage {
     size_t zero_off = 0, zero_bytes = 0;  // region to zero once (hdr, tickets, flags)
 };
 
+// Scratch that outlives one launch: counters, tickets and flags that the
+// kernels return to zero, results the kernel writes in place (may be pinned
+// host memory mapped for the device), and where the error word is published.
+struct ExternalScratch {
+    uint32_t* hdr = nullptr;       // H_WORDS words, zero
+    uint32_t* tickets = nullptr;   // task_cap words, zero
+    uint32_t* flags = nullptr;     // task_cap words, zero
+    size_t task_cap = 0;
+    scl_result* results = nullptr; // task_cap results (device-usable address)
+    uint32_t* err_out = nullptr;   // device-usable address, written at kernel end
+};
+
 // Lay out `p` in a new arena block; fill `host` with the bytes to upload
-// (plan_bytes long) with result pointers set; fill `args`.
-int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, KernelArgs* args);
+// (plan_bytes long) with result pointers set; fill `args`.  With `ext`, the
+// counters, results and error word live there instead of in the block, and
+// nothing in the block needs zeroing.
+int build_image(Ctx* c, Plan& p, PlanImage* img, std::vector<char>* host, KernelArgs* args,
+                const ExternalScratch* ext = nullptr);
 
 // Launch a planned image (persistent kernel, then the keyed fold if needed).
 int launch_plan(Ctx* c, const Plan& p, const KernelArgs& args, cudaStream_t st);

@@ -34,10 +34,26 @@ int Server::start(Ctx* c, const scl_server_config* in) {
     SCL_CUDA(cudaSetDevice(c->device));
     SCL_CUDA(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
     slots.resize(cfg.inflight_batches);
+    const size_t cap = cfg.max_batch_tasks;
     for (auto& s : slots) {
         SCL_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
         SCL_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+        SCL_CUDA(cudaHostAlloc((void**)&s.h_res, (cap + 1) * sizeof(scl_result),
+                               cudaHostAllocMapped));
+        SCL_CUDA(cudaHostGetDevicePointer((void**)&s.d_res, s.h_res, 0));
+        const size_t zb = align_up(H_WORDS * 4) + 2 * align_up(cap * 4);
+        s.zero = c->arena.alloc(zb);
+        if (!s.zero) return fail(SCL_E_NOMEM, "arena: no room for the server's scratch");
+        SCL_CUDA(cudaMemset(s.zero, 0, zb));
+        char* z = static_cast<char*>(s.zero);
+        s.ext.hdr = reinterpret_cast<uint32_t*>(z);
+        s.ext.tickets = reinterpret_cast<uint32_t*>(z + align_up(H_WORDS * 4));
+        s.ext.flags = reinterpret_cast<uint32_t*>(z + align_up(H_WORDS * 4) + align_up(cap * 4));
+        s.ext.task_cap = cap;
+        s.ext.results = s.d_res;
+        s.ext.err_out = reinterpret_cast<uint32_t*>(s.d_res + cap);
     }
+    SCL_CUDA(cudaDeviceSynchronize());
     memset(&stats, 0, sizeof stats);
     stats.budget_bytes = budget;
     stopping = false;
@@ -62,6 +78,7 @@ void Server::stop() {
         if (s.done) cudaEventDestroy(s.done);
         if (s.h_plan) cudaFreeHost(s.h_plan);
         if (s.h_res) cudaFreeHost(s.h_res);
+        if (s.zero) ctx->arena.release(s.zero);
         s = Slot();
     }
     if (copy_stream) cudaStreamDestroy(copy_stream);
@@ -135,6 +152,7 @@ void Server::admit_locked() {
         admitted.push_back(std::move(t));
         waiting.pop_front();
     }
+    admitted_n.store(admitted.size(), std::memory_order_release);
 }
 
 int Server::submit(SrvTask&& t, uint64_t* ticket) {
@@ -161,6 +179,15 @@ void Server::batcher_loop() {
     cudaSetDevice(ctx->device);
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
+        // Spin up to 100 us for new work before sleeping: a condition-variable
+        // wake-up costs more than most batches take on the GPU.
+        if (admitted.empty() && !stopping) {
+            lk.unlock();
+            const int64_t t0 = now_ns();
+            while (admitted_n.load(std::memory_order_acquire) == 0 && now_ns() - t0 < 100000) {
+            }
+            lk.lock();
+        }
         Slot* free_slot = nullptr;
         cv_work.wait(lk, [&] {
             free_slot = nullptr;
@@ -179,6 +206,7 @@ void Server::batcher_loop() {
         s.tasks.assign(std::make_move_iterator(admitted.begin()),
                        std::make_move_iterator(admitted.begin() + take));
         admitted.erase(admitted.begin(), admitted.begin() + take);
+        admitted_n.store(admitted.size(), std::memory_order_release);
         lk.unlock();
         const int st = launch_slot(s);
         lk.lock();
@@ -205,7 +233,7 @@ int Server::launch_slot(Slot& s) {
         s.plan = Plan();
         s.img = PlanImage();
         SCL_TRY(plan_tasks(ctx, tv.data(), n, &s.plan));
-        SCL_TRY(build_image(ctx, s.plan, &s.img, &host, &s.args));
+        SCL_TRY(build_image(ctx, s.plan, &s.img, &host, &s.args, &s.ext));
     }
     if (s.h_plan_cap < host.size()) {
         if (s.h_plan) cudaFreeHost(s.h_plan);
@@ -213,25 +241,14 @@ int Server::launch_slot(Slot& s) {
         s.h_plan_cap = std::max<size_t>(host.size(), 1 << 20);
         SCL_CUDA(cudaHostAlloc((void**)&s.h_plan, s.h_plan_cap, cudaHostAllocDefault));
     }
-    if (s.h_res_cap < n + 1) {
-        if (s.h_res) cudaFreeHost(s.h_res);
-        s.h_res = nullptr;
-        s.h_res_cap = std::max<size_t>(n + 1, 1024);
-        SCL_CUDA(cudaHostAlloc((void**)&s.h_res, s.h_res_cap * sizeof(scl_result),
-                               cudaHostAllocDefault));
-    }
     memcpy(s.h_plan, host.data(), host.size());
+    // one upload; counters are already zero, results come back by themselves
     SCL_CUDA(cudaMemcpyAsync(s.img.block, s.h_plan, s.img.plan_bytes, cudaMemcpyHostToDevice,
                              s.stream));
-    SCL_CUDA(cudaMemsetAsync((char*)s.img.block + s.img.zero_off, 0, s.img.zero_bytes, s.stream));
     for (auto& t : s.tasks)
         if (t.ready) SCL_CUDA(cudaStreamWaitEvent(s.stream, t.ready, 0));
     s.t_launch = now_ns();
     SCL_TRY(launch_plan(ctx, s.plan, s.args, s.stream));
-    SCL_CUDA(cudaMemcpyAsync(s.h_res, s.img.results, n * sizeof(scl_result),
-                             cudaMemcpyDeviceToHost, s.stream));
-    SCL_CUDA(cudaMemcpyAsync(s.h_res + n, s.img.hdr + H_ERROR, 4, cudaMemcpyDeviceToHost,
-                             s.stream));
     SCL_CUDA(cudaEventRecord(s.done, s.stream));
     {
         std::lock_guard<std::mutex> g(mu);
@@ -244,7 +261,13 @@ void Server::finish_slot(Slot& s, int status) {
     const int64_t t = now_ns();
     const uint32_t n = (uint32_t)s.tasks.size();
     uint32_t err = 0;
-    if (status == SCL_OK && s.h_res) memcpy(&err, s.h_res + n, 4);
+    if (status == SCL_OK) memcpy(&err, s.h_res + s.ext.task_cap, 4);
+    if (err || status != SCL_OK) {
+        // a failed launch may have left counters set: clear them before reuse
+        const size_t zb = align_up(H_WORDS * 4) + 2 * align_up(s.ext.task_cap * 4);
+        cudaMemset(s.zero, 0, zb);
+        cudaDeviceSynchronize();
+    }
     std::vector<Done> ds(n);
     for (uint32_t i = 0; i < n; ++i) {
         Done& d = ds[i];

@@ -54,8 +54,14 @@ struct Slot {
     KernelArgs args;
     char* h_plan = nullptr;     // pinned staging for the plan upload
     size_t h_plan_cap = 0;
-    scl_result* h_res = nullptr;   // pinned results (+ one slot for the error word)
-    size_t h_res_cap = 0;
+    // Results land here straight from the kernel: pinned host memory the
+    // device writes through its mapped address; entry [cap] holds the error
+    // word.  Counters, tickets and flags stay in `zero`, which the kernels
+    // return to zero after every launch, so a launch needs no memset.
+    scl_result* h_res = nullptr;
+    scl_result* d_res = nullptr;   // device address of h_res
+    void* zero = nullptr;          // arena block: hdr | tickets | flags
+    ExternalScratch ext;
     int64_t t_launch = 0;
 };
 
@@ -72,6 +78,7 @@ struct Server {
     std::condition_variable cv_work, cv_done;
     std::deque<SrvTask> waiting;    // not admitted yet
     std::deque<SrvTask> admitted;   // admitted, not launched
+    std::atomic<size_t> admitted_n{0};   // admitted.size(), readable without the lock
     std::vector<Slot> slots;
     std::unordered_map<uint64_t, Done> done;
     uint64_t next_ticket = 1;
