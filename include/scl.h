@@ -385,7 +385,7 @@ int scl_set_shape(scl_ctx* ctx, int family, const scl_shape* shape);
 
 /* Autotuner configuration; every field may be 0 for its default. */
 typedef struct {
-    uint64_t probe_bytes;   /* bytes of the large probe partitions (256 MiB)     */
+    uint64_t probe_bytes;   /* bytes read by each probe batch (512 MiB)          */
     uint32_t reps;          /* timed launches per candidate (10)                 */
     uint32_t families;      /* bit (1 << SCL_FAMILY_*) per family to tune (all)  */
 } scl_autotune_config;
@@ -397,14 +397,18 @@ typedef struct {
 } scl_autotune_report;
 
 /* Choose each family's launch shape by measurement: block size, items per
- * thread, CTAs per SM, load path and TMA ring depth.  Probe partitions
- * (a few large, 512 of 16,384 elements) are filled on the device in the
- * arena and every compiled candidate is timed with CUDA events on `stream`;
- * the fastest (sum of both probe batches) is kept.  The FP32 family is tuned
- * first; MIXED inherits its block and items per thread.  If the context has a
- * tune cache path, the result is written there and loaded by later contexts
- * on a GPU with the same SM count.  cfg and report may be NULL.  Takes about a
- * second; the arena needs about 4 x probe_bytes free (the probe shrinks to
+ * thread, CTAs per SM, load path and TMA ring depth.  Two probe batches are
+ * filled on the device in the arena -- four large partitions, and uneven
+ * partitions with log-normal sizes (median 16,384, sigma 1.5) -- each reading
+ * probe_bytes (larger than the L2 by default); every compiled candidate is
+ * timed with CUDA events on `stream` (best of three rounds of `reps`
+ * launches) and the candidate with the smallest sum of (time / best time)
+ * over the probes is kept.  The FP32 family is tuned first and its candidates
+ * are also scored on a mixed batch, because MIXED inherits its block and
+ * items per thread; MIXED then tunes CTAs per SM.  If the context has a tune
+ * cache path, the result is written there and loaded by later contexts on a
+ * GPU with the same SM count.  cfg and report may be NULL.  Takes a few
+ * seconds; the arena needs about 8 x probe_bytes free (the probe shrinks to
  * fit, down to 16 MiB).  Errors: SCL_E_NOMEM, SCL_E_CUDA, SCL_E_TIMEOUT. */
 int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
                  scl_autotune_report* report);

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "runtime.h"
@@ -84,16 +85,23 @@ int time_tasks(Ctx* c, const std::vector<scl_task>& tasks, cudaStream_t st, uint
             st_ok = fail(SCL_E_CUDA, "autotune: event create failed");
             break;
         }
-        cudaEventRecord(e0, st);
-        for (uint32_t r = 0; r < reps && st_ok == SCL_OK; ++r) st_ok = launch_plan(c, p, args, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st_ok = fail(SCL_E_CUDA, "autotune: probe launch failed");
-            break;
+        // the best of three rounds of `reps` back-to-back launches
+        double best = 1e30;
+        for (int round = 0; round < 3 && st_ok == SCL_OK; ++round) {
+            cudaEventRecord(e0, st);
+            for (uint32_t r = 0; r < reps && st_ok == SCL_OK; ++r)
+                st_ok = launch_plan(c, p, args, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st_ok = fail(SCL_E_CUDA, "autotune: probe launch failed");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, (double)t / reps);
         }
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        *ms = t / reps;
+        if (st_ok != SCL_OK) break;
+        *ms = best;
         uint32_t err = 0;
         cudaMemcpy(&err, img.hdr + H_ERROR, 4, cudaMemcpyDeviceToHost);
         if (err) st_ok = fail(SCL_E_TIMEOUT, "autotune: device error word 0x%x", err);
@@ -125,21 +133,45 @@ std::vector<Shape> candidates(int family, const Shape& f32) {
 
 }  // namespace
 
+// Deterministic log-normal partition sizes (median `med`, sigma 1.5, clipped
+// to [256, 64 * med]) summing to at most `total`: the shape of a batch of
+// uneven partitions.  splitmix64 + Box-Muller, so every run probes the same.
+static std::vector<uint64_t> lognormal_probe_sizes(uint64_t total, uint64_t med) {
+    std::vector<uint64_t> out;
+    uint64_t x = 0x5eedull, used = 0;
+    auto next = [&]() {
+        uint64_t z = (x += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return ((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+    };
+    while (out.size() < 16384) {
+        const double u1 = std::max(next(), 1e-12), u2 = next();
+        const double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+        uint64_t n = (uint64_t)std::floor(std::exp(std::log((double)med) + 1.5 * g));
+        n = std::min<uint64_t>(std::max<uint64_t>(n, 256), 64 * med);
+        n = (n + 63) / 64 * 64;   // keep every partition 256-byte aligned
+        if (used + n > total) break;
+        out.push_back(n);
+        used += n;
+    }
+    return out;
+}
+
 int autotune(Ctx* c, const scl_autotune_config* cfg, cudaStream_t st, scl_autotune_report* rep) {
-    uint64_t probe = cfg && cfg->probe_bytes ? cfg->probe_bytes : (256ull << 20);
+    uint64_t probe = cfg && cfg->probe_bytes ? cfg->probe_bytes : (512ull << 20);
     const uint32_t reps = cfg && cfg->reps ? cfg->reps : 10;
     const uint32_t fams = cfg && cfg->families ? cfg->families : 0xfu;
-    const uint64_t small_n = 16384, small_parts = 512;
-    // room: u32 + f32 + keys + vals regions, plus keyed output tables
+    // four regions (u32, f32, keys, values) of 2 * probe bytes each: a large
+    // probe and a log-normal many-partition probe, each reading `probe` bytes
     const uint64_t room = c->arena.largest_free();
-    while (probe > (16ull << 20) && 4 * (probe + small_n * small_parts * 4) + (64ull << 20) > room)
-        probe /= 2;
-    const uint64_t nbig = probe / 4;                     // elements of the big region
-    const uint64_t n = nbig + small_n * small_parts;     // elements per region
+    while (probe > (16ull << 20) && 8 * probe + (64ull << 20) > room) probe /= 2;
+    const uint64_t P = probe / 4;                 // elements per probe
+    const uint64_t n = 2 * P;                     // elements per region
     const uint64_t region = align_up(n * 4);
     char* buf = (char*)c->arena.alloc(4 * region);
-    const uint32_t nkeyed_out = 8 + (uint32_t)small_parts;
-    uint32_t* kout = (uint32_t*)c->arena.alloc((size_t)nkeyed_out * kKeyedTableWords * 4);
+    const uint32_t ntables = 64;                  // keyed output tables, shared round-robin
+    uint32_t* kout = (uint32_t*)c->arena.alloc((size_t)ntables * kKeyedTableWords * 4);
     if (!buf || !kout) {
         c->arena.release(buf);
         c->arena.release(kout);
@@ -154,67 +186,84 @@ int autotune(Ctx* c, const scl_autotune_config* cfg, cudaStream_t st, scl_autotu
                      ? SCL_OK
                      : fail(SCL_E_CUDA, "autotune: probe fill failed");
 
-    // probe batches per family: 4 big partitions + small_parts small ones
     std::vector<scl_part> reg;
     std::vector<scl_task> big[M_NUM], small[M_NUM];
-    auto table = [&](uint32_t i) { return kout + (size_t)i * kKeyedTableWords; };
     uint32_t kt = 0;
-    for (int b = 0; b < 4; ++b) {
-        const uint64_t off = b * (nbig / 4), len = nbig / 4;
+    auto table = [&]() { return kout + (size_t)(kt++ % ntables) * kKeyedTableWords; };
+    auto add_set = [&](std::vector<scl_task>* dst, uint64_t off, uint64_t len) {
         scl_part pu = add_part(c, SCL_U32, U + off, nullptr, len);
-        scl_part pf = add_part(c, SCL_F32, F + off, nullptr, len / 2 * 2);
+        scl_part pf = add_part(c, SCL_F32, F + off, nullptr, len);
         scl_part pk = add_part(c, SCL_KV_I32_F32, K + off / 2, V + off / 2, len / 2);
         reg.insert(reg.end(), {pu, pf, pk});
-        big[M_U32].push_back(make_task(pu, SCL_K_MIX32, SCL_R_SUM, nullptr, nullptr));
-        big[M_F32].push_back(make_task(pf, SCL_K_POLY3, SCL_R_SUM_MIN_MAX, nullptr, nullptr));
-        uint32_t* tb = table(kt++);
-        big[M_KEYED].push_back(make_task(pk, SCL_K_IDENT, SCL_R_KEYED_COUNT_SUM, tb,
+        dst[M_U32].push_back(make_task(pu, SCL_K_MIX32, SCL_R_SUM, nullptr, nullptr));
+        dst[M_F32].push_back(make_task(pf, SCL_K_POLY3, SCL_R_SUM_MIN_MAX, nullptr, nullptr));
+        uint32_t* tb = table();
+        dst[M_KEYED].push_back(make_task(pk, SCL_K_IDENT, SCL_R_KEYED_COUNT_SUM, tb,
                                          (float*)(tb + kMaxKeys)));
+    };
+    // large probe: 4 partitions of P/4 elements (P/8 pairs for keyed)
+    for (int b = 0; b < 4; ++b) add_set(big, b * (P / 4), P / 4);
+    // many-partition probe: log-normal sizes, median 16 Ki (scaled down for
+    // small probes), the uneven-batch workload
+    const uint64_t med = std::min<uint64_t>(16384, std::max<uint64_t>(1024, P / 2048));
+    uint64_t off = P;
+    for (uint64_t len : lognormal_probe_sizes(P, med)) {
+        add_set(small, off, len);
+        off += len;
     }
-    for (uint64_t s = 0; s < small_parts; ++s) {
-        const uint64_t off = nbig + s * small_n;
-        scl_part pu = add_part(c, SCL_U32, U + off, nullptr, small_n);
-        scl_part pf = add_part(c, SCL_F32, F + off, nullptr, small_n);
-        scl_part pk = add_part(c, SCL_KV_I32_F32, K + off, V + off, small_n);
-        reg.insert(reg.end(), {pu, pf, pk});
-        small[M_U32].push_back(make_task(pu, SCL_K_MIX32, SCL_R_SUM, nullptr, nullptr));
-        small[M_F32].push_back(make_task(pf, SCL_K_POLY3, SCL_R_SUM_MIN_MAX, nullptr, nullptr));
-        uint32_t* tb = table(kt++ % nkeyed_out);
-        small[M_KEYED].push_back(make_task(pk, SCL_K_IDENT, SCL_R_KEYED_COUNT_SUM, tb,
-                                           (float*)(tb + kMaxKeys)));
-    }
-    // mixed: a third of each
+    // mixed batches: a third of each kind
     for (int m = 0; m < 3; ++m) {
         big[M_ALL].push_back(big[m][0]);
-        for (uint64_t s = m; s < small_parts; s += 3) small[M_ALL].push_back(small[m][s]);
+        for (size_t i = m; i < small[m].size(); i += 3) small[M_ALL].push_back(small[m][i]);
     }
 
     if (rep) memset(rep, 0, sizeof *rep);
+    // fp32 first: mixed batches inherit its block and items per thread, so its
+    // candidates are also scored on the mixed many-partition probe
     const int order[M_NUM] = {M_F32, M_U32, M_KEYED, M_ALL};
     for (int oi = 0; oi < M_NUM && status == SCL_OK; ++oi) {
         const int fam = order[oi];
         if (!(fams & (1u << fam))) continue;
         const Shape keep = c->shape[fam];
-        Shape best = keep;
-        double best_ms = 1e30;
-        uint32_t tried = 0;
-        for (const Shape& s : candidates(fam, c->shape[M_F32])) {
-            c->shape[fam] = s;
-            double t_big = 0, t_small = 0;
-            int r = time_tasks(c, big[fam], st, reps, &t_big);
-            if (r == SCL_OK) r = time_tasks(c, small[fam], st, reps, &t_small);
+        const std::vector<Shape> cand = candidates(fam, c->shape[M_F32]);
+        std::vector<std::vector<double>> t(cand.size());   // per candidate, per probe
+        for (size_t ci = 0; ci < cand.size() && status == SCL_OK; ++ci) {
+            c->shape[fam] = cand[ci];
+            double tb = 0, ts = 0, tm = 0;
+            int r = time_tasks(c, big[fam], st, reps, &tb);
+            if (r == SCL_OK) r = time_tasks(c, small[fam], st, reps, &ts);
+            if (r == SCL_OK && fam == M_F32) r = time_tasks(c, small[M_ALL], st, reps, &tm);
             if (r == SCL_E_TIMEOUT || r == SCL_E_CUDA) {
                 status = r;
                 break;
             }
             if (r != SCL_OK) continue;
-            ++tried;
-            if (t_big + t_small < best_ms) {
-                best_ms = t_big + t_small;
-                best = s;
+            t[ci] = fam == M_F32 ? std::vector<double>{tb, ts, tm} : std::vector<double>{tb, ts};
+        }
+        // objective: sum over probes of time / the best time on that probe
+        size_t best = cand.size();
+        double best_score = 1e30, best_ms = 0;
+        uint32_t tried = 0;
+        if (status == SCL_OK) {
+            std::vector<double> lo(3, 1e30);
+            for (auto& v : t)
+                for (size_t k = 0; k < v.size(); ++k) lo[k] = std::min(lo[k], v[k]);
+            for (size_t ci = 0; ci < cand.size(); ++ci) {
+                if (t[ci].empty()) continue;
+                ++tried;
+                double score = 0, ms = 0;
+                for (size_t k = 0; k < t[ci].size(); ++k) {
+                    score += t[ci][k] / lo[k];
+                    ms += t[ci][k];
+                }
+                if (score < best_score) {
+                    best_score = score;
+                    best = ci;
+                    best_ms = ms;
+                }
             }
         }
-        c->shape[fam] = status == SCL_OK ? best : keep;
+        c->shape[fam] = (status == SCL_OK && best < cand.size()) ? cand[best] : keep;
         if (rep) {
             const Shape sh = c->shape_for(fam);
             const KernelEntry* e = find_entry(fam, sh);

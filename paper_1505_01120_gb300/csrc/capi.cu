@@ -111,8 +111,10 @@ int scl_create(const scl_config* cfg, scl_ctx** out) {
     c->d_kout = (uint32_t*)c->arena.alloc((size_t)kMaxKeys * 16);
     int st = SCL_OK;
     if (!c->d_result || !c->d_kout) st = fail(SCL_E_NOMEM, "arena too small");
-    if (st == SCL_OK && cudaHostAlloc((void**)&c->h_result, 2 * sizeof(scl_result),
-                                      cudaHostAllocDefault) != cudaSuccess)
+    if (st == SCL_OK && (cudaHostAlloc((void**)&c->h_result, 2 * sizeof(scl_result),
+                                       cudaHostAllocMapped) != cudaSuccess ||
+                         cudaHostGetDevicePointer((void**)&c->dh_result, c->h_result, 0) !=
+                             cudaSuccess))
         st = fail(SCL_E_CUDA, "cudaHostAlloc failed");
     if (st == SCL_OK) st = ensure_scratch(c, &c->single, 1, 0, 0, kMaxKeys / kFoldBlock);
     if (st == SCL_OK && cfg->tune_cache_path) {
@@ -349,14 +351,15 @@ int scl_map_into(scl_ctx* ctx, scl_part in, scl_map_kernel kernel, const float c
 
 static int map_reduce_common(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
                              const float coef[3], scl_reduce reduce, void* stream,
-                             scl_result* dev_out) {
+                             scl_result* dev_out, uint32_t* err_out = nullptr) {
     const Partition* p = ctx->part(part);
     if (!p) return fail(SCL_E_INVALID, "unknown partition handle");
     uint32_t kind;
     if (reduce == SCL_R_KEYED_COUNT_SUM)
         return fail(SCL_E_UNSUPPORTED, "use scl_keyed_reduce for keyed partitions");
     SCL_TRY(resolve_kind(p->dtype, kernel, reduce, &kind));
-    return run_single(ctx, *p, kind, coef, 0, nullptr, nullptr, nullptr, dev_out, S(stream));
+    return run_single(ctx, *p, kind, coef, 0, nullptr, nullptr, nullptr, dev_out, S(stream),
+                      err_out);
 }
 
 // After a synchronous single call: a non-zero device error word means a
@@ -385,8 +388,12 @@ int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const flo
                    scl_reduce reduce, void* stream, scl_result* out) {
     CTX_ENTER(ctx);
     if (!out) return fail(SCL_E_INVALID, "null output");
-    SCL_TRY(map_reduce_common(ctx, part, kernel, coef, reduce, stream, ctx->d_result));
-    SCL_TRY(fetch_single(ctx, S(stream)));
+    // The kernel writes the result and the error word straight into pinned
+    // host memory (its mapped address): no copies, one synchronisation.
+    SCL_TRY(map_reduce_common(ctx, part, kernel, coef, reduce, stream, ctx->dh_result,
+                              reinterpret_cast<uint32_t*>(ctx->dh_result + 1)));
+    SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    SCL_TRY(check_single_error(ctx));
     *out = *ctx->h_result;
     return SCL_OK;
 }

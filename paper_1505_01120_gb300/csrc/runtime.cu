@@ -320,7 +320,7 @@ static int launch_entry(const KernelEntry* e, uint32_t grid, const KernelArgs& a
 
 int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uint32_t nk,
                uint32_t* counts, float* sums, double* sums64, scl_result* dres,
-               cudaStream_t st) {
+               cudaStream_t st, uint32_t* err_out) {
     const int mask = mask_of_kind(kind);
     const Shape sh = c->shape_for(mask);
     const KernelEntry* e = find_entry(mask, sh);
@@ -356,6 +356,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     a.tickets = c->single.tickets;
     a.task_flags = c->single.flags;
     a.hdr = c->single.hdr;
+    a.err_out = err_out;
     SCL_TRY(launch_entry(e, grid, a, st));
     if (is_keyed(kind) && t.nseg > 1) {
         const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;

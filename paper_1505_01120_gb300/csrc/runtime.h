@@ -197,7 +197,8 @@ struct Ctx {
     std::map<const void*, int> occ_cache;
     Scratch single;
     scl_result* d_result = nullptr;        // single-call result slot
-    scl_result* h_result = nullptr;        // pinned
+    scl_result* h_result = nullptr;        // pinned, mapped: [0] result, [1] error word
+    scl_result* dh_result = nullptr;       // device address of h_result
     uint32_t* d_kout = nullptr;            // single-call keyed outputs (counts|sums|sums64)
     uint32_t* d_large = nullptr;           // large-key reduce: ticket, bad-key flag
     std::string tune_path;
@@ -216,7 +217,8 @@ void fill_task(DevTask* t, const Partition& p, uint32_t kind, const float* coef,
 
 // Single-partition launch (scl_map_reduce*, scl_keyed_reduce*).
 int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uint32_t nk,
-               uint32_t* counts, float* sums, double* sums64, scl_result* dres, cudaStream_t st);
+               uint32_t* counts, float* sums, double* sums64, scl_result* dres, cudaStream_t st,
+               uint32_t* err_out = nullptr);
 
 // Global count of kernel launches made by the library (graph replays included).
 void count_launches(uint64_t n);
