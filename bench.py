@@ -386,21 +386,33 @@ def serve_config(torch, scl, ctx, stream, full: bool) -> dict:
         arr = scl.make_tasks([tasks[i] for i in pick])
         mean_bytes = float(np.mean([int(sizes[i]) * (8 if kinds[i] == 2 else 4) for i in pick]))
         row = {"tasks": n, "offered_gbs": rate * mean_bytes / 1e9}
-        for mode, k, mb in (("batched", 4, 4096), ("unbatched", 1, 1)):
-            scl.scl_server_start(ctx.handle, inflight_batches=k, max_batch_tasks=mb,
-                                 hbm_budget_bytes=120 * 10**9)
-            t0 = time.perf_counter()
-            lat, res = scl.scl_server_replay(ctx.handle, arr, arrivals, n)
-            wall = time.perf_counter() - t0 - 1e-3
-            st = scl.scl_server_get_stats(ctx.handle)
-            scl.scl_server_stop(ctx.handle)
+        for mode, k, mb in (("batched", 4, 4096), ("unbatched", 1, 1), ("device_polled", 0, 0)):
+            if mode == "device_polled":
+                scl.scl_devserver_start(ctx.handle)
+                t0 = time.perf_counter()
+                lat, res = scl.scl_devserver_replay(ctx.handle, arr, arrivals, n)
+                wall = time.perf_counter() - t0 - 1e-3
+                st = scl.scl_devserver_get_stats(ctx.handle)
+                scl.scl_devserver_stop(ctx.handle)
+                extra = {"kernel_launches": int(st["kernel_launches"]),
+                         "idle_stops": int(st["idle_stops"]),
+                         "device_errors": int(st["device_errors"]),
+                         "max_inflight": int(st["max_inflight"]), "grid": int(st["grid"])}
+            else:
+                scl.scl_server_start(ctx.handle, inflight_batches=k, max_batch_tasks=mb,
+                                     hbm_budget_bytes=120 * 10**9)
+                t0 = time.perf_counter()
+                lat, res = scl.scl_server_replay(ctx.handle, arr, arrivals, n)
+                wall = time.perf_counter() - t0 - 1e-3
+                st = scl.scl_server_get_stats(ctx.handle)
+                scl.scl_server_stop(ctx.handle)
+                extra = {"batches": int(st["batches"]), "max_batch": int(st["max_batch"])}
             ok = bool(np.all(res["status"] == 0))
             row[mode] = {"tasks_per_s": n / wall, "p50_us": float(np.percentile(lat, 50)) / 1e3,
                          "p99_us": float(np.percentile(lat, 99)) / 1e3,
                          "p999_us": float(np.percentile(lat, 99.9)) / 1e3,
-                         "batches": int(st["batches"]), "max_batch": int(st["max_batch"]),
-                         "all_ok": ok}
-            if mode == "batched":
+                         **extra, "all_ok": ok}
+            if mode != "unbatched":
                 # spot check a served uint32 result against the oracle
                 j = next(j for j in range(n) if kinds[pick[j]] == synth.KIND_MIX32)
                 h = bufs[pick[j]][0].cpu().numpy().view(np.uint32)
@@ -408,6 +420,37 @@ def serve_config(torch, scl, ctx, stream, full: bool) -> dict:
         out["rates"][str(rate)] = row
     for t in tasks:
         scl.scl_free_partition(ctx.handle, t["part"])
+    out["round_trip_1x1048576_mix32"] = round_trip(torch, scl, ctx)
+    return out
+
+
+def round_trip(torch, scl, ctx) -> dict:
+    """Closed loop, one job at a time: submit a 1,048,576-element mix32 job and
+    wait for its result on the host, through each server."""
+    b = torch.randint(-2**31, 2**31 - 1, (1 << 20,), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    q = scl.scl_wrap_device(ctx.handle, b.data_ptr(), None, scl.SCL_U32, 1 << 20)
+    arr = scl.make_tasks([dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_SUM)])
+    out = {}
+
+    def loop(submit, wait):
+        lat = []
+        for i in range(300):
+            t0 = time.perf_counter()
+            wait(submit())
+            if i >= 20:
+                lat.append((time.perf_counter() - t0) * 1e6)
+        return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99))}
+
+    scl.scl_server_start(ctx.handle, inflight_batches=4, max_batch_tasks=4096)
+    out["batched_server"] = loop(lambda: scl.scl_server_submit(ctx.handle, arr, 0),
+                                 lambda t: scl.scl_server_wait(ctx.handle, t))
+    scl.scl_server_stop(ctx.handle)
+    scl.scl_devserver_start(ctx.handle)
+    out["device_polled_server"] = loop(lambda: scl.scl_devserver_submit(ctx.handle, arr, 0),
+                                       lambda t: scl.scl_devserver_wait(ctx.handle, t))
+    scl.scl_devserver_stop(ctx.handle)
+    scl.scl_free_partition(ctx.handle, q)
     return out
 
 

@@ -550,6 +550,98 @@ int scl_server_stop(scl_ctx* ctx);
 int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s,
                       uint32_t n, int64_t* latency_ns, scl_result* results);
 
+/* ------------------------------------------------------ device-polling server */
+
+/* The device-polling server: the same offload of partition tasks as the
+ * continuous-batching server, with no kernel launch per batch.  One kernel
+ * stays resident on the GPU; scl_devserver_submit writes the task as a job
+ * into pinned host memory the kernel reads through its mapped address and
+ * then advances a published-work count (the doorbell); the kernel's CTAs
+ * claim the job's work units (streaming segments, keyed pieces) from a
+ * device counter, run them and write the result and a done word into pinned
+ * host memory, where a driver thread hands it out.  The paper runs each
+ * partition task through its worker's accelerator, one at a time per device
+ * (Sec. 3.1.1-3.1.5); it has no device-resident dispatcher.
+ *
+ * Results: uint32 and fp32 tasks give bitwise the result scl_map_reduce gives
+ * with the fp32 family's (block, items per thread) -- the same segment code;
+ * keyed tasks give exact counts and fp64-accumulated sums (float atomics make
+ * their last bits depend on timing, as in the batch kernels).
+ *
+ * Waits are bounded.  The host ends the kernel after idle_stop_ns without
+ * work (and launches it again with the next job).  In the kernel, a CTA
+ * waiting for the doorbell gives up after wait_limit_ns (or an iteration
+ * limit if the GPU timer stalls), sets an error word in host memory and
+ * returns; a job descriptor that fails the kernel's bounds checks does the
+ * same.  The driver then ends the kernel, fails the jobs in flight with
+ * status SCL_E_TIMEOUT, zeroes the device state and carries on
+ * (device_errors counts these).
+ *
+ * While the kernel is resident it holds the SMs: other launches on the
+ * device start as its CTAs leave, i.e. idle_stop_ns after its last job or at
+ * scl_devserver_stop.  Partitions and keyed output arrays referenced by jobs
+ * must stay alive until the jobs complete. */
+typedef struct {
+    uint32_t job_ring;        /* jobs in flight (0 = 16384)                      */
+    uint32_t unit_ring;       /* work units in flight, also streaming partial
+                                 slots (0 = 1048576)                             */
+    uint32_t keyed_slots;     /* multi-piece keyed jobs in flight (0 = 256)      */
+    int32_t ctas_per_sm;      /* resident CTAs per SM (0 = as many as fit)       */
+    uint64_t idle_stop_ns;    /* end the kernel after this long without work
+                                 (0 = 2 ms; UINT64_MAX = never: the device wait
+                                 limit then ends it, as an error)                */
+    uint64_t wait_limit_ns;   /* longest device wait for the doorbell (0 = 1 s)  */
+    uint64_t reserved[2];
+} scl_devserver_config;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t kernel_launches;  /* resident-kernel instances started             */
+    uint64_t idle_stops;       /* instances ended by the host after idling      */
+    uint64_t device_errors;    /* instances ended by a device wait limit or a
+                                  failed descriptor check                       */
+    uint64_t units;            /* work units published                          */
+    uint64_t ring_waits;       /* jobs that waited for ring space               */
+    uint64_t max_inflight;     /* most jobs in flight at once                   */
+    uint32_t grid, block;      /* launch shape of the resident kernel           */
+    uint32_t items_per_thread, reserved0;
+    uint64_t reserved[3];
+} scl_devserver_stats;
+
+/* Start the device-polling server on this context (the kernel is launched
+ * with the first job).  Takes about (unit_ring x 32 + keyed_slots x 48 Ki)
+ * bytes of the arena and 7 MB of pinned host memory at the defaults.
+ * Errors: SCL_E_STATE (already running), SCL_E_INVALID, SCL_E_NOMEM,
+ * SCL_E_UNSUPPORTED (no compiled kernel for the fp32 family's shape). */
+int scl_devserver_start(scl_ctx* ctx, const scl_devserver_config* cfg);
+
+/* Submit one task on a resident partition; returns at once with a ticket.
+ * Thread-safe.  Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED, SCL_E_BUDGET (more
+ * work units than the rings hold), SCL_E_STATE (not running), SCL_E_CUDA
+ * (the server met a CUDA error and stopped taking work). */
+int scl_devserver_submit(scl_ctx* ctx, const scl_task* task, uint64_t* ticket);
+
+/* SCL_OK and the result once done (the ticket is then retired), SCL_E_PENDING
+ * before.  A failed job has its status in out->status. */
+int scl_devserver_poll(scl_ctx* ctx, uint64_t ticket, scl_result* out);
+
+/* Block until the job is done or timeout_ms passes (SCL_E_TIMEOUT). */
+int scl_devserver_wait(scl_ctx* ctx, uint64_t ticket, uint32_t timeout_ms,
+                       scl_result* out);
+
+int scl_devserver_get_stats(scl_ctx* ctx, scl_devserver_stats* out);
+
+/* Finish the jobs in flight, end the kernel, release the server.  No-op if
+ * not running.  Called by scl_destroy. */
+int scl_devserver_stop(scl_ctx* ctx);
+
+/* Open-loop trace driver, as scl_server_replay: submit tasks[i] at
+ * arrival_s[i] seconds after the start, then wait for all (each wait bounded
+ * by 60 s, else SCL_E_TIMEOUT).  latency_ns[i] = completion seen by the host
+ * - scheduled arrival (may be NULL); results[i] (may be NULL). */
+int scl_devserver_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s,
+                         uint32_t n, int64_t* latency_ns, scl_result* results);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "runtime.h"
+#include "devserver.h"
 #include "server.h"
 
 namespace scl {
@@ -131,10 +132,12 @@ int scl_create(const scl_config* cfg, scl_ctx** out) {
 }
 
 int scl_server_stop(scl_ctx* ctx);
+int scl_devserver_stop(scl_ctx* ctx);
 
 int scl_destroy(scl_ctx* ctx) {
     if (!ctx) return SCL_OK;
     scl_server_stop(ctx);
+    scl_devserver_stop(ctx);
     {
         std::lock_guard<std::recursive_mutex> g(ctx->mu);
         cudaSetDevice(ctx->device);

@@ -1,0 +1,105 @@
+// devserver.h -- host side of the device-polling server (k_doorbell).
+//
+// Jobs are published, not launched: submit() writes the job descriptor and
+// its unit -> job entries into pinned host memory and advances the doorbell;
+// the resident kernel picks the units up.  A driver thread watches the done
+// words, hands out results, publishes jobs that waited for ring space, ends
+// the kernel after idle_stop_ns without work, and recovers when the device
+// reports an error (its wait limit ran out, or a descriptor failed a check):
+// it stops the kernel, fails the jobs still in flight with SCL_E_TIMEOUT,
+// zeroes the device state and carries on.  A kernel instance is launched
+// whenever work is published and none is running.
+#pragma once
+
+#include <map>
+#include <set>
+
+#include "server.h"
+
+namespace scl {
+
+// First-fit allocator of index ranges [0, cap) (partial slots).
+class RangeAlloc {
+  public:
+    void init(uint32_t cap) {
+        free_.clear();
+        if (cap) free_[0] = cap;
+    }
+    bool alloc(uint32_t n, uint32_t* off);
+    void release(uint32_t off, uint32_t n);
+
+  private:
+    std::map<uint32_t, uint32_t> free_;   // offset -> length
+};
+
+struct DbInflight {
+    uint64_t ticket = 0;
+    uint32_t seq = 0;
+    uint32_t nseg = 0;
+    uint64_t unit0 = 0;
+    uint32_t spart0 = UINT32_MAX;   // partial range (streaming, nseg > 1)
+    uint32_t kslot = UINT32_MAX;    // keyed accumulator (keyed, nseg > 1)
+    uint64_t n = 0;
+    uint32_t kind = 0;
+    int64_t t_submit = 0;
+};
+
+struct DbPending {
+    uint64_t ticket = 0;
+    DevTask t{};
+    int64_t t_submit = 0;
+};
+
+struct DevServer {
+    Ctx* ctx = nullptr;
+    scl_devserver_config cfg{};
+    const void* fn = nullptr;
+    int block = 0, ipt = 0;
+    uint32_t grid = 0;
+    cudaStream_t stream = nullptr;
+
+    // pinned host memory, mapped: header | jobs | unit -> job | results | done
+    char* hblock = nullptr;
+    DbHost* hh = nullptr;
+    DbJob* hjobs = nullptr;
+    uint32_t* hunit = nullptr;
+    scl_result* hres = nullptr;
+    uint32_t* hdone = nullptr;
+    scl_result* dres = nullptr;   // device address of hres
+    // arena block: state | tickets | flags | keyed accumulators | partials
+    void* dblock = nullptr;
+    size_t zero_small = 0;        // state + tickets + flags
+    size_t zero_all = 0;          // ... + keyed accumulators
+    DbArgs args{};
+
+    std::mutex mu;
+    std::condition_variable cv_done, cv_work;
+    std::deque<DbPending> queue;             // waiting for ring space
+    std::vector<DbInflight> ring;            // by job ring index
+    std::vector<uint32_t> free_ring, free_kslots, inflight;
+    std::multiset<uint64_t> unit0s;          // first units of jobs in flight
+    RangeAlloc spart;
+    uint64_t units = 0;                      // published in this kernel instance
+    uint32_t next_seq = 1;
+    bool running = false, broken = false, quitting = false;
+    int64_t last_activity = 0, last_progress = 0;
+    std::unordered_map<uint64_t, Done> done;
+    uint64_t next_ticket = 1;
+    scl_devserver_stats stats{};
+    std::thread driver;
+
+    ~DevServer();
+    int start(Ctx* c, const scl_devserver_config* cfg);
+    int submit(const scl_task& task, const Partition& p, int64_t t_submit, uint64_t* ticket);
+    void stop();
+
+  private:
+    bool publish_locked(DbPending& p);
+    int launch_locked();
+    int end_kernel_locked(bool zero_all_state);
+    void complete_locked(uint32_t j, const scl_result& r, int64_t now);
+    void recover_locked(int status);
+    void driver_loop();
+};
+
+}  // namespace scl

@@ -174,6 +174,64 @@ struct LargeKeyedArgs {
     uint32_t* bad;            // zeroed before the launch
 };
 
+// Device-polling server.  The host publishes jobs in pinned host memory that
+// the device reads through its mapped address; a resident kernel claims work
+// units (streaming segments or keyed pieces) from a device counter and waits,
+// bounded, for the host's published-unit count (the doorbell) to cover them.
+constexpr uint64_t kDbKeyedPiece = 65536;     // pairs per keyed piece (at least)
+constexpr uint32_t kDbMaxKeyedPieces = 4096;
+constexpr uint32_t kDbAccWords = kMaxKeys * 3; // keyed accumulator: u32 count, f64 sum
+
+enum DbErr : uint32_t { DB_ERR_WAIT = 1u, DB_ERR_DESC = 2u };
+
+struct alignas(16) DbJob {     // 128 bytes, host memory
+    DevTask t;                 // result: mapped host slot; slot0: partial range or accumulator
+    uint64_t unit0;            // first unit of the job in this kernel instance's numbering
+    uint32_t seq;              // written to done[ring] once the result is in place
+    uint32_t ring;             // job ring index (tickets, flags, results, done)
+    uint32_t pad[4];
+};
+static_assert(sizeof(DbJob) == 128, "DbJob layout");
+
+struct alignas(128) DbHost {   // pinned host memory, mapped
+    unsigned long long tail;   // units published (host writes, release)
+    uint32_t pad0[30];
+    uint32_t stop;             // host: stop once no published unit is left
+    uint32_t pad1[31];
+    uint32_t err;              // device: DbErr bits
+    uint32_t pad2[31];
+};
+
+struct alignas(128) DbState {  // device memory, zero at every kernel start
+    unsigned long long next;   // claim counter
+    uint32_t pad0[30];
+    unsigned long long tail;   // device mirror of DbHost::tail
+    uint32_t stop;             // device mirror of DbHost::stop
+    uint32_t lock;             // one CTA at a time reads the host words
+    uint32_t pad1[28];
+};
+
+struct DbArgs {
+    KernelArgs ka;              // spart, tickets, task_flags of the job ring
+    DbHost* host;               // device address of the mapped header
+    const DbJob* jobs;          // [job_ring], mapped
+    const uint32_t* unit_job;   // [unit_ring] unit -> job ring index, mapped
+    uint32_t* done;             // [job_ring], mapped
+    DbState* state;
+    uint32_t* kacc;             // [kacc_slots][kDbAccWords]: count[kMaxKeys] u32, sum[kMaxKeys] f64
+    unsigned long long wait_limit_ns;
+    unsigned long long max_polls;
+    uint32_t job_ring, unit_ring, spart_cap, kacc_slots;
+};
+
+// Keyed pieces of a device-polled keyed job of n pairs.
+__host__ __device__ inline uint32_t db_keyed_pieces(uint64_t n) {
+    uint64_t g = (n + kDbKeyedPiece - 1) / kDbKeyedPiece;
+    if (g < 1) g = 1;
+    if (g > kDbMaxKeyedPieces) g = kDbMaxKeyedPieces;
+    return (uint32_t)g;
+}
+
 // Host-side launch entry of one compiled persistent-kernel instantiation.
 struct KernelEntry {
     int mask, block, ipt;              // block = threads that touch data (consumers)
@@ -196,5 +254,6 @@ extern int map_kernel_ipt();
 extern const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k);
 extern const void* large_keyed_kernel_fn(int aligned);
 extern const void* large_keyed_finish_fn();
+extern const void* doorbell_kernel_fn(int block, int ipt);
 
 }  // namespace scl

@@ -159,8 +159,9 @@ __device__ __forceinline__ void write_result(scl_result* r, uint64_t u, double s
 // c + 4*(j*BLOCK + t) + {0..3} for j < IPT -- the same mapping in the vector
 // path and in the masked scalar path (ragged tail, or an unaligned
 // partition), so the fp32 grouping of a chunk never depends on the path.
+// Returns true in thread 0 of the CTA that wrote the task's final result.
 template <int BLOCK, int IPT, int KIND>
-__device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTask& t,
+__device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTask& t,
                                                uint32_t task, uint32_t local, RedSmem& sm) {
     constexpr bool F32 = (KIND == K_F32_IDENT || KIND == K_F32_POLY3);
     constexpr uint32_t CH = BLOCK * IPT * 4;
@@ -246,7 +247,7 @@ __device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTas
     if (t.nseg == 1) {
         if (threadIdx.x == 0)
             write_result(t.result, usum, dsum, F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, t.n, t.kind);
-        return;
+        return threadIdx.x == 0;
     }
     if (threadIdx.x == 0) {
         StreamPartial* sp = a.spart + t.slot0 + local;
@@ -259,7 +260,7 @@ __device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTas
         sm.flag = (prev == t.nseg - 1) ? 1u : 0u;
     }
     __syncthreads();
-    if (sm.flag == 0) return;   // uniform across the CTA
+    if (sm.flag == 0) return false;   // uniform across the CTA
     __threadfence();
 
     // This CTA finished the task's last segment: fold the partials in slot order.
@@ -285,6 +286,7 @@ __device__ __forceinline__ void stream_segment(const KernelArgs& a, const DevTas
         write_result(t.result, fu, fs, F32 ? fmn : 0.f, F32 ? fmx : 0.f, SCL_OK, t.n, t.kind);
         a.tickets[task] = 0u;   // ready for the next launch
     }
+    return threadIdx.x == 0;
 }
 
 // ------------------------------------------------------------ keyed piece
@@ -301,13 +303,12 @@ __device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, u
     }
 }
 
-// One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
-// shared-memory table (count, fp32 sum) and written to the outputs (single
-// piece) or to partial slot slot0 + slot.
+// Pairs [b, e) of a keyed task accumulated into the CTA's shared-memory table
+// (count[kMaxKeys] then fp32 sum[kMaxKeys]), zeroed first.  Returns, in every
+// thread, whether any key was out of range.  Ends with a barrier.
 template <int BLOCK, int IPT, bool HASHED>
-__device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
-                                            uint32_t slot, uint64_t b, uint64_t e,
-                                            uint32_t* tab, RedSmem& sm) {
+__device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, uint64_t e,
+                                                uint32_t* tab) {
     constexpr uint32_t CH = BLOCK * IPT * 4;
     uint32_t* cnt = tab;
     float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
@@ -350,8 +351,22 @@ __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& 
                                       ld_stream_b32(vb + (g + q) * 4), nk, cnt, sum, bad);
         }
     }
-    const int any_bad = __syncthreads_or((int)bad);
+    return __syncthreads_or((int)bad);
+}
 
+// One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
+// shared-memory table (count, fp32 sum) and written to the outputs (single
+// piece) or to partial slot slot0 + slot.  Returns true in thread 0 if it
+// wrote the task's result (single piece).
+template <int BLOCK, int IPT, bool HASHED>
+__device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
+                                            uint32_t slot, uint64_t b, uint64_t e,
+                                            uint32_t* tab, RedSmem& sm) {
+    const int any_bad = keyed_accumulate<BLOCK, IPT, HASHED>(t, b, e, tab);
+    const uint32_t* cnt = tab;
+    const float* sum = reinterpret_cast<const float*>(tab + kMaxKeys);
+    const uint32_t nk = t.num_keys;
+    bool wrote = false;
     if (t.nseg == 1) {
         unsigned long long ctot = 0;
         double stot = 0.0;
@@ -367,9 +382,11 @@ __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& 
         float dummy0 = CUDART_INF_F, dummy1 = -CUDART_INF_F;
         block_reduce_f<BLOCK>(stot, dummy0, dummy1, sm);
         ctot = block_sum_u64<BLOCK>(ctot, sm);
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             write_result(t.result, ctot, stot, CUDART_INF_F, -CUDART_INF_F,
                          any_bad ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
+            wrote = true;
+        }
     } else {
         uint32_t* dst = a.kpart + (size_t)(t.slot0 + slot) * kKeyedTableWords;
         for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
@@ -379,6 +396,7 @@ __device__ __forceinline__ void keyed_piece(const KernelArgs& a, const DevTask& 
         if (any_bad && threadIdx.x == 0) atomicOr(&a.task_flags[task], 1u);
     }
     __syncthreads();   // the table is re-zeroed by the next piece
+    return wrote;
 }
 
 // ------------------------------------------------------- persistent kernel

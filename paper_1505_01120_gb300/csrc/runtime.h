@@ -178,6 +178,7 @@ int launch_plan(Ctx* c, const Plan& p, const KernelArgs& args, cudaStream_t st);
 // ---------------------------------------------------------------- context
 
 struct Server;
+struct DevServer;
 
 struct Ctx {
     int device = 0;
@@ -203,6 +204,7 @@ struct Ctx {
     uint32_t* d_large = nullptr;           // large-key reduce: ticket, bad-key flag
     std::string tune_path;
     std::unique_ptr<Server> server;
+    std::unique_ptr<DevServer> devserver;
 
     const Partition* part(scl_part h) const {
         auto it = parts.find(h);

@@ -89,6 +89,25 @@ class scl_server_stats(ctypes.Structure):
         "peak_bytes_in_use")]
 
 
+class scl_devserver_config(ctypes.Structure):
+    _fields_ = [("job_ring", ctypes.c_uint32), ("unit_ring", ctypes.c_uint32),
+                ("keyed_slots", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_int32),
+                ("idle_stop_ns", ctypes.c_uint64), ("wait_limit_ns", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 2)]
+
+
+class scl_devserver_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "completed", "failed", "kernel_launches", "idle_stops", "device_errors",
+        "units", "ring_waits", "max_inflight")] + [
+        ("grid", ctypes.c_uint32), ("block", ctypes.c_uint32),
+        ("items_per_thread", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint64 * 3)]
+
+
+IDLE_STOP_NEVER = (1 << 64) - 1
+
+
 class scl_task(ctypes.Structure):
     _fields_ = [("part", ctypes.c_uint64), ("kernel", ctypes.c_int32),
                 ("reduce", ctypes.c_int32), ("num_keys", ctypes.c_uint32),
@@ -179,6 +198,13 @@ _SIGS = {
     "scl_server_get_stats": ([_P, ctypes.POINTER(scl_server_stats)], ctypes.c_int),
     "scl_server_stop": ([_P], ctypes.c_int),
     "scl_server_replay": ([_P, _P, _P, _u32, _P, _P], ctypes.c_int),
+    "scl_devserver_start": ([_P, ctypes.POINTER(scl_devserver_config)], ctypes.c_int),
+    "scl_devserver_submit": ([_P, _P, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_devserver_poll": ([_P, _u64, ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_devserver_wait": ([_P, _u64, _u32, ctypes.POINTER(scl_result)], ctypes.c_int),
+    "scl_devserver_get_stats": ([_P, ctypes.POINTER(scl_devserver_stats)], ctypes.c_int),
+    "scl_devserver_stop": ([_P], ctypes.c_int),
+    "scl_devserver_replay": ([_P, _P, _P, _u32, _P, _P], ctypes.c_int),
     "scl_map_reduce_noalloc": ([_P, ctypes.c_int, _u64, ctypes.c_int, _P, ctypes.c_int, _P, _P],
                                ctypes.c_int),
 }
@@ -511,6 +537,61 @@ def scl_server_replay(ctx: int, tasks: ctypes.Array, arrival_s: np.ndarray, n: i
     res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
     st = lib.scl_server_replay(ctx, ctypes.cast(tasks, ctypes.c_void_p), arr.ctypes.data, n,
                                lat.ctypes.data, res.ctypes.data)
+    if not allow_errors:
+        _check(st)
+    return lat[:n], res[:n]
+
+
+def scl_devserver_start(ctx: int, job_ring: int = 0, unit_ring: int = 0, keyed_slots: int = 0,
+                        ctas_per_sm: int = 0, idle_stop_ns: int = 0,
+                        wait_limit_ns: int = 0) -> None:
+    cfg = scl_devserver_config(job_ring=job_ring, unit_ring=unit_ring, keyed_slots=keyed_slots,
+                               ctas_per_sm=ctas_per_sm, idle_stop_ns=idle_stop_ns,
+                               wait_limit_ns=wait_limit_ns)
+    _check(lib.scl_devserver_start(ctx, ctypes.byref(cfg)))
+
+
+def scl_devserver_submit(ctx: int, tasks: ctypes.Array, index: int = 0) -> int:
+    t = _u64()
+    _check(lib.scl_devserver_submit(ctx, ctypes.byref(tasks[index]), ctypes.byref(t)))
+    return t.value
+
+
+def scl_devserver_poll(ctx: int, ticket: int):
+    """The result, or None while the job is pending."""
+    r = scl_result()
+    st = lib.scl_devserver_poll(ctx, ticket, ctypes.byref(r))
+    if st == SCL_E_PENDING:
+        return None
+    _check(st)
+    return r
+
+
+def scl_devserver_wait(ctx: int, ticket: int, timeout_ms: int = 60_000) -> scl_result:
+    r = scl_result()
+    _check(lib.scl_devserver_wait(ctx, ticket, timeout_ms, ctypes.byref(r)))
+    return r
+
+
+def scl_devserver_get_stats(ctx: int) -> dict:
+    s = scl_devserver_stats()
+    _check(lib.scl_devserver_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in scl_devserver_stats._fields_
+            if not k.startswith("reserved")}
+
+
+def scl_devserver_stop(ctx: int) -> None:
+    _check(lib.scl_devserver_stop(ctx))
+
+
+def scl_devserver_replay(ctx: int, tasks: ctypes.Array, arrival_s: np.ndarray, n: int,
+                         allow_errors: bool = False):
+    """Returns (latency_ns int64[n], results RESULT_DTYPE[n])."""
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.zeros(max(1, n), dtype=np.int64)
+    res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
+    st = lib.scl_devserver_replay(ctx, ctypes.cast(tasks, ctypes.c_void_p), arr.ctypes.data, n,
+                                  lat.ctypes.data, res.ctypes.data)
     if not allow_errors:
         _check(st)
     return lat[:n], res[:n]

@@ -58,6 +58,9 @@ def test_struct_layouts_match_header(scl):
     assert scl.scl_result.f64_sum.offset == 8 and scl.scl_result.n.offset == 32
     assert scl.scl_task.coef.offset == 20 and scl.scl_task.counts_out.offset == 32
     assert scl.scl_abi_version() == 1
+    assert ctypes.sizeof(scl.scl_devserver_config) == 48
+    assert ctypes.sizeof(scl.scl_devserver_stats) == 112
+    assert scl.scl_devserver_stats.grid.offset == 72
 
 
 def test_status_text(scl):
