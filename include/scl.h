@@ -609,8 +609,9 @@ typedef struct {
 } scl_devserver_stats;
 
 /* Start the device-polling server on this context (the kernel is launched
- * with the first job).  Takes about (unit_ring x 32 + keyed_slots x 48 Ki)
- * bytes of the arena and 7 MB of pinned host memory at the defaults.
+ * with the first job).  Takes unit_ring x 32 + keyed_slots x 48 Ki +
+ * job_ring x 140 bytes of the arena (47 MB at the defaults) and job_ring x 180
+ * + unit_ring x 8 bytes of pinned host memory (11 MB).
  * Errors: SCL_E_STATE (already running), SCL_E_INVALID, SCL_E_NOMEM,
  * SCL_E_UNSUPPORTED (no compiled kernel for the fp32 family's shape). */
 int scl_devserver_start(scl_ctx* ctx, const scl_devserver_config* cfg);

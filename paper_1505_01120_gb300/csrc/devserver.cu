@@ -10,7 +10,7 @@ static_assert(sizeof(scl_devserver_stats) == 112, "scl_devserver_stats layout");
 
 namespace scl {
 
-static_assert(sizeof(DbState) == 256 && sizeof(DbHost) == 384, "doorbell header layout");
+static_assert(sizeof(DbState) == 384 && sizeof(DbHost) == 384, "doorbell header layout");
 
 const void* doorbell_kernel_256(int ipt);
 const void* doorbell_kernel_512(int ipt);
@@ -90,10 +90,9 @@ int DevServer::start(Ctx* c, const scl_devserver_config* in) {
     grid = (uint32_t)(c->sms * per);
     SCL_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
 
-    // pinned host block: header | jobs | unit -> job | results | done
+    // pinned host block: header | jobs | results | done
     const size_t o_jobs = sizeof(DbHost);
-    const size_t o_unit = o_jobs + (size_t)cfg.job_ring * sizeof(DbJob);
-    const size_t o_res = align_up(o_unit + (size_t)cfg.unit_ring * 4, 128);
+    const size_t o_res = align_up(o_jobs + (size_t)cfg.job_ring * sizeof(DbJob), 128);
     const size_t o_done = align_up(o_res + (size_t)cfg.job_ring * sizeof(scl_result), 128);
     const size_t hbytes = o_done + (size_t)cfg.job_ring * 4;
     SCL_CUDA(cudaHostAlloc((void**)&hblock, hbytes, cudaHostAllocMapped));
@@ -102,22 +101,24 @@ int DevServer::start(Ctx* c, const scl_devserver_config* in) {
     SCL_CUDA(cudaHostGetDevicePointer((void**)&dh, hblock, 0));
     hh = reinterpret_cast<DbHost*>(hblock);
     hjobs = reinterpret_cast<DbJob*>(hblock + o_jobs);
-    hunit = reinterpret_cast<uint32_t*>(hblock + o_unit);
     hres = reinterpret_cast<scl_result*>(hblock + o_res);
     hdone = reinterpret_cast<uint32_t*>(hblock + o_done);
     dres = reinterpret_cast<scl_result*>(dh + o_res);
 
-    // arena block: state | tickets | flags | keyed accumulators | partials
+    // arena block: state | tickets | flags | keyed accumulators | job copies |
+    // unit map | partials
     const size_t d_tick = align_up(sizeof(DbState));
     const size_t d_flag = d_tick + align_up((size_t)cfg.job_ring * 4);
     const size_t d_kacc = d_flag + align_up((size_t)cfg.job_ring * 4);
-    const size_t d_spart = d_kacc + align_up((size_t)cfg.keyed_slots * kDbAccWords * 4);
+    const size_t d_djobs = d_kacc + align_up((size_t)cfg.keyed_slots * kDbAccWords * 4);
+    const size_t d_dunit = d_djobs + align_up((size_t)cfg.job_ring * sizeof(DbJob));
+    const size_t d_spart = d_dunit + align_up((size_t)cfg.unit_ring * 4);
     const size_t dbytes = d_spart + (size_t)cfg.unit_ring * sizeof(StreamPartial);
     dblock = c->arena.alloc(dbytes);
     if (!dblock)
         return fail(SCL_E_NOMEM, "arena: no room for the device-polling server (%zu bytes)", dbytes);
     zero_small = sizeof(DbState);
-    zero_all = d_spart;
+    zero_all = d_djobs;   // the job copies and unit map are written before they are read
     SCL_CUDA(cudaMemsetAsync(dblock, 0, zero_all, stream));
     SCL_CUDA(cudaStreamSynchronize(stream));
     char* db = static_cast<char*>(dblock);
@@ -127,10 +128,11 @@ int DevServer::start(Ctx* c, const scl_devserver_config* in) {
     args.ka.task_flags = reinterpret_cast<uint32_t*>(db + d_flag);
     args.host = reinterpret_cast<DbHost*>(dh);
     args.jobs = reinterpret_cast<const DbJob*>(dh + o_jobs);
-    args.unit_job = reinterpret_cast<const uint32_t*>(dh + o_unit);
     args.done = reinterpret_cast<uint32_t*>(dh + o_done);
     args.state = reinterpret_cast<DbState*>(db);
     args.kacc = reinterpret_cast<uint32_t*>(db + d_kacc);
+    args.djobs = reinterpret_cast<DbJob*>(db + d_djobs);
+    args.dunit = reinterpret_cast<uint32_t*>(db + d_dunit);
     args.wait_limit_ns = cfg.wait_limit_ns;
     args.max_polls = cfg.wait_limit_ns / 16 + 4096;   // a backstop if the GPU timer stalls
     args.job_ring = cfg.job_ring;
@@ -139,8 +141,6 @@ int DevServer::start(Ctx* c, const scl_devserver_config* in) {
     args.kacc_slots = cfg.keyed_slots;
 
     ring.assign(cfg.job_ring, DbInflight{});
-    free_ring.clear();
-    for (uint32_t j = cfg.job_ring; j-- > 0;) free_ring.push_back(j);
     free_kslots.clear();
     for (uint32_t k = cfg.keyed_slots; k-- > 0;) free_kslots.push_back(k);
     spart.init(cfg.unit_ring);
@@ -198,13 +198,17 @@ int DevServer::submit(const scl_task& task, const Partition& p, int64_t t_submit
     return SCL_OK;
 }
 
-// Write the job and its unit entries, then advance the doorbell.
+// Write job `pubs` into its ring slot, then ring the doorbell.
 bool DevServer::publish_locked(DbPending& q) {
     const uint32_t nseg = q.t.nseg;
     const bool keyed = is_keyed(q.t.kind);
-    if (free_ring.empty()) return false;
-    const uint64_t lo = unit0s.empty() ? units : *unit0s.begin();
-    if (units + nseg - lo > cfg.unit_ring) return false;   // unit entries still unread
+    if (!inflight_pubs.empty()) {
+        // the slot of job pubs - job_ring must be free, and the unit map
+        // entries of jobs in flight must not be overwritten
+        const auto& oldest = *inflight_pubs.begin();
+        if (pubs - oldest.first >= cfg.job_ring) return false;
+        if (units + nseg - oldest.second > cfg.unit_ring) return false;
+    }
     uint32_t sp = UINT32_MAX, ks = UINT32_MAX;
     if (nseg > 1) {
         if (keyed) {
@@ -215,8 +219,7 @@ bool DevServer::publish_locked(DbPending& q) {
             return false;
         }
     }
-    const uint32_t j = free_ring.back();
-    free_ring.pop_back();
+    const uint32_t j = (uint32_t)(pubs % cfg.job_ring);
     const uint32_t seq = next_seq++;
     if (next_seq == 0) next_seq = 1;
 
@@ -230,21 +233,23 @@ bool DevServer::publish_locked(DbPending& q) {
     job.ring = j;
     hjobs[j] = job;
     hdone[j] = 0;
-    for (uint32_t i = 0; i < nseg; ++i) hunit[(units + i) % cfg.unit_ring] = j;
     DbInflight& f = ring[j];
     f.ticket = q.ticket;
     f.seq = seq;
     f.nseg = nseg;
     f.unit0 = units;
+    f.pub = pubs;
     f.spart0 = sp;
     f.kslot = ks;
     f.n = q.t.n;
     f.kind = q.t.kind;
     f.t_submit = q.t_submit;
+    inflight_pubs[pubs] = units;
     units += nseg;
-    store_release(&hh->tail, (unsigned long long)units);   // the doorbell
+    ++pubs;
+    store_release(&hh->jobs, (unsigned long long)pubs);   // the doorbell
+    pub_gen.fetch_add(1, std::memory_order_release);
 
-    unit0s.insert(f.unit0);
     inflight.push_back(j);
     stats.units += nseg;
     stats.max_inflight = std::max<uint64_t>(stats.max_inflight, inflight.size());
@@ -294,10 +299,11 @@ int DevServer::end_kernel_locked(bool zero_all_state) {
         broken = true;
         return fail(SCL_E_CUDA, "device-polling server: state reset failed");
     }
-    store_release(&hh->tail, 0ull);
+    store_release(&hh->jobs, 0ull);
     store_release(&hh->stop, 0u);
     store_release(&hh->err, 0u);
     units = 0;
+    pubs = 0;
     return SCL_OK;
 }
 
@@ -310,10 +316,38 @@ void DevServer::complete_locked(uint32_t j, const scl_result& r, int64_t now) {
     done[f.ticket] = d;
     if (f.spart0 != UINT32_MAX) spart.release(f.spart0, f.nseg);
     if (f.kslot != UINT32_MAX) free_kslots.push_back(f.kslot);
-    unit0s.erase(unit0s.find(f.unit0));
-    free_ring.push_back(j);
+    inflight_pubs.erase(f.pub);
     f = DbInflight{};
     last_activity = now;
+    done_gen.fetch_add(1, std::memory_order_release);
+}
+
+bool DevServer::wait_done(uint64_t ticket, int64_t spin_ns, int64_t timeout_ns, Done* out) {
+    const int64_t t0 = now_ns();
+    std::unique_lock<std::mutex> lk(mu);
+    uint64_t seen = done_gen.load(std::memory_order_acquire);
+    for (;;) {
+        auto it = done.find(ticket);
+        if (it != done.end()) {
+            *out = it->second;
+            done.erase(it);
+            return true;
+        }
+        const int64_t now = now_ns();
+        if (now - t0 >= timeout_ns) return false;
+        if (now - t0 < spin_ns) {
+            // spin without the lock until some job completes
+            lk.unlock();
+            while (done_gen.load(std::memory_order_acquire) == seen && now_ns() - t0 < spin_ns) {
+            }
+            lk.lock();
+            seen = done_gen.load(std::memory_order_acquire);
+            continue;
+        }
+        cv_done.wait_for(lk, std::chrono::nanoseconds(std::min<int64_t>(timeout_ns - (now - t0),
+                                                                      1000000)));
+        seen = done_gen.load(std::memory_order_acquire);
+    }
 }
 
 // End the kernel after a device error (or a CUDA error), hand out what
@@ -337,8 +371,10 @@ void DevServer::recover_locked(int status) {
         stats.failed++;
     }
     inflight.clear();
-    unit0s.clear();
+    inflight_pubs.clear();
     spart.init(cfg.unit_ring);
+    free_kslots.clear();
+    for (uint32_t k = cfg.keyed_slots; k-- > 0;) free_kslots.push_back(k);
     if (broken) {
         for (auto& q : queue) {
             Done d;
@@ -355,6 +391,7 @@ void DevServer::recover_locked(int status) {
 }
 
 void DevServer::driver_loop() {
+    std::vector<std::pair<uint32_t, uint32_t>> watch;   // (ring index, seq) in flight
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         bool progress = false;
@@ -404,8 +441,24 @@ void DevServer::driver_loop() {
         }
         if (progress) continue;
         if (!inflight.empty()) {
+            // watch the done words of the jobs in flight without the lock, until
+            // one completes, a job is published, the device reports an error,
+            // or 50 us pass (the other checks above run again)
+            watch.clear();
+            for (uint32_t j : inflight) watch.emplace_back(j, ring[j].seq);
+            const uint64_t gen = pub_gen.load(std::memory_order_acquire);
             lk.unlock();
-            std::this_thread::yield();
+            const int64_t until = now_ns() + 50000;
+            for (bool hit = false; !hit;) {
+                for (const auto& w : watch)
+                    if (load_acquire(&hdone[w.first]) == w.second) {
+                        hit = true;
+                        break;
+                    }
+                if (pub_gen.load(std::memory_order_acquire) != gen ||
+                    load_acquire(&hh->err) != 0u || now_ns() > until)
+                    break;
+            }
             lk.lock();
         } else if (running) {
             cv_work.wait_for(lk, std::chrono::microseconds(50));
@@ -505,16 +558,16 @@ int scl_devserver_poll(scl_ctx* ctx, uint64_t ticket, scl_result* out) {
 int scl_devserver_wait(scl_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, scl_result* out) {
     DevServer* s = nullptr;
     SCL_TRY(dsrv_of(ctx, &s));
-    std::unique_lock<std::mutex> lk(s->mu);
-    if (ticket == 0 || ticket >= s->next_ticket)
-        return fail(SCL_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
-    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
-                                        [&] { return s->done.count(ticket) > 0; });
-    if (!ok) return fail(SCL_E_TIMEOUT, "ticket %llu not done after %u ms",
-                         (unsigned long long)ticket, timeout_ms);
-    auto it = s->done.find(ticket);
-    if (out) *out = it->second.r;
-    s->done.erase(it);
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (ticket == 0 || ticket >= s->next_ticket)
+            return fail(SCL_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    }
+    Done d;
+    if (!s->wait_done(ticket, 200000, (int64_t)timeout_ms * 1000000, &d))
+        return fail(SCL_E_TIMEOUT, "ticket %llu not done after %u ms",
+                    (unsigned long long)ticket, timeout_ms);
+    if (out) *out = d.r;
     return SCL_OK;
 }
 
@@ -562,15 +615,12 @@ int scl_devserver_replay(scl_ctx* ctx, const scl_task* tasks, const double* arri
     for (uint32_t i = 0; i < n; ++i) {
         int st = sub_status[i];
         if (st == SCL_OK) {
-            std::unique_lock<std::mutex> lk(s->mu);
-            if (!s->cv_done.wait_for(lk, std::chrono::seconds(60),
-                                     [&] { return s->done.count(tickets[i]) > 0; })) {
+            Done d;
+            if (!s->wait_done(tickets[i], 0, 60000000000ll, &d)) {
                 st = fail(SCL_E_TIMEOUT, "task %u not done after 60 s", i);
             } else {
-                auto it = s->done.find(tickets[i]);
-                if (latency_ns) latency_ns[i] = it->second.t_done - sched[i];
-                if (results) results[i] = it->second.r;
-                s->done.erase(it);
+                if (latency_ns) latency_ns[i] = d.t_done - sched[i];
+                if (results) results[i] = d.r;
                 continue;
             }
         }

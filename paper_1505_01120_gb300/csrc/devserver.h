@@ -1,8 +1,8 @@
 // devserver.h -- host side of the device-polling server (k_doorbell).
 //
-// Jobs are published, not launched: submit() writes the job descriptor and
-// its unit -> job entries into pinned host memory and advances the doorbell;
-// the resident kernel picks the units up.  A driver thread watches the done
+// Jobs are published, not launched: submit() writes job p's descriptor into
+// ring slot p % job_ring of pinned host memory and raises the count of
+// published jobs (the doorbell); the resident kernel picks the job up.  A driver thread watches the done
 // words, hands out results, publishes jobs that waited for ring space, ends
 // the kernel after idle_stop_ns without work, and recovers when the device
 // reports an error (its wait limit ran out, or a descriptor failed a check):
@@ -12,7 +12,6 @@
 #pragma once
 
 #include <map>
-#include <set>
 
 #include "server.h"
 
@@ -37,6 +36,7 @@ struct DbInflight {
     uint32_t seq = 0;
     uint32_t nseg = 0;
     uint64_t unit0 = 0;
+    uint64_t pub = 0;               // publication index
     uint32_t spart0 = UINT32_MAX;   // partial range (streaming, nseg > 1)
     uint32_t kslot = UINT32_MAX;    // keyed accumulator (keyed, nseg > 1)
     uint64_t n = 0;
@@ -58,11 +58,10 @@ struct DevServer {
     uint32_t grid = 0;
     cudaStream_t stream = nullptr;
 
-    // pinned host memory, mapped: header | jobs | unit -> job | results | done
+    // pinned host memory, mapped: header | jobs | results | done
     char* hblock = nullptr;
     DbHost* hh = nullptr;
     DbJob* hjobs = nullptr;
-    uint32_t* hunit = nullptr;
     scl_result* hres = nullptr;
     uint32_t* hdone = nullptr;
     scl_result* dres = nullptr;   // device address of hres
@@ -75,22 +74,28 @@ struct DevServer {
     std::mutex mu;
     std::condition_variable cv_done, cv_work;
     std::deque<DbPending> queue;             // waiting for ring space
-    std::vector<DbInflight> ring;            // by job ring index
-    std::vector<uint32_t> free_ring, free_kslots, inflight;
-    std::multiset<uint64_t> unit0s;          // first units of jobs in flight
+    std::vector<DbInflight> ring;            // by job ring slot (publication index % job_ring)
+    std::vector<uint32_t> free_kslots, inflight;
+    std::map<uint64_t, uint64_t> inflight_pubs;   // publication index -> first unit
     RangeAlloc spart;
-    uint64_t units = 0;                      // published in this kernel instance
+    uint64_t pubs = 0;                       // jobs published in this kernel instance
+    uint64_t units = 0;                      // their units
     uint32_t next_seq = 1;
     bool running = false, broken = false, quitting = false;
     int64_t last_activity = 0, last_progress = 0;
     std::unordered_map<uint64_t, Done> done;
     uint64_t next_ticket = 1;
+    std::atomic<uint64_t> pub_gen{0};    // bumped by every publish
+    std::atomic<uint64_t> done_gen{0};   // bumped by every completion
     scl_devserver_stats stats{};
     std::thread driver;
 
     ~DevServer();
     int start(Ctx* c, const scl_devserver_config* cfg);
     int submit(const scl_task& task, const Partition& p, int64_t t_submit, uint64_t* ticket);
+    // Wait for a ticket: spin (lock released) up to spin_ns, then block.
+    // True with the result taken out; false on timeout.
+    bool wait_done(uint64_t ticket, int64_t spin_ns, int64_t timeout_ns, Done* out);
     void stop();
 
   private:

@@ -176,25 +176,30 @@ struct LargeKeyedArgs {
 
 // Device-polling server.  The host publishes jobs in pinned host memory that
 // the device reads through its mapped address; a resident kernel claims work
-// units (streaming segments or keyed pieces) from a device counter and waits,
-// bounded, for the host's published-unit count (the doorbell) to cover them.
+// units (streaming segments or keyed pieces) from a device counter.  Jobs are
+// published in order: job p sits in ring slot p % job_ring, its units follow
+// those of job p - 1, and the host's doorbell is the count of jobs published.
+// One CTA at a time reads the doorbell and expands new jobs into device
+// memory (descriptor copy, unit -> slot map) before it raises the device's
+// count of available units; every other CTA reads only device memory.
 constexpr uint64_t kDbKeyedPiece = 65536;     // pairs per keyed piece (at least)
 constexpr uint32_t kDbMaxKeyedPieces = 4096;
 constexpr uint32_t kDbAccWords = kMaxKeys * 3; // keyed accumulator: u32 count, f64 sum
+constexpr uint32_t kDbMaxExpand = 64;          // jobs expanded per doorbell read
 
 enum DbErr : uint32_t { DB_ERR_WAIT = 1u, DB_ERR_DESC = 2u };
 
-struct alignas(16) DbJob {     // 128 bytes, host memory
+struct alignas(16) DbJob {     // 128 bytes, host memory (and its device copy)
     DevTask t;                 // result: mapped host slot; slot0: partial range or accumulator
     uint64_t unit0;            // first unit of the job in this kernel instance's numbering
     uint32_t seq;              // written to done[ring] once the result is in place
-    uint32_t ring;             // job ring index (tickets, flags, results, done)
+    uint32_t ring;             // p % job_ring (tickets, flags, results, done)
     uint32_t pad[4];
 };
 static_assert(sizeof(DbJob) == 128, "DbJob layout");
 
 struct alignas(128) DbHost {   // pinned host memory, mapped
-    unsigned long long tail;   // units published (host writes, release)
+    unsigned long long jobs;   // jobs published (host writes, release): the doorbell
     uint32_t pad0[30];
     uint32_t stop;             // host: stop once no published unit is left
     uint32_t pad1[31];
@@ -205,19 +210,23 @@ struct alignas(128) DbHost {   // pinned host memory, mapped
 struct alignas(128) DbState {  // device memory, zero at every kernel start
     unsigned long long next;   // claim counter
     uint32_t pad0[30];
-    unsigned long long tail;   // device mirror of DbHost::tail
+    unsigned long long tail;   // units expanded (available to claim)
     uint32_t stop;             // device mirror of DbHost::stop
-    uint32_t lock;             // one CTA at a time reads the host words
-    uint32_t pad1[28];
+    uint32_t pad1[29];
+    uint32_t lock;             // held by the CTA reading the doorbell
+    uint32_t pad2;
+    unsigned long long jobs_seen;   // jobs expanded (lock holder only)
+    uint32_t pad3[28];
 };
 
 struct DbArgs {
     KernelArgs ka;              // spart, tickets, task_flags of the job ring
     DbHost* host;               // device address of the mapped header
     const DbJob* jobs;          // [job_ring], mapped
-    const uint32_t* unit_job;   // [unit_ring] unit -> job ring index, mapped
     uint32_t* done;             // [job_ring], mapped
     DbState* state;
+    DbJob* djobs;               // [job_ring] device copies of the descriptors
+    uint32_t* dunit;            // [unit_ring] unit -> ring slot of its job
     uint32_t* kacc;             // [kacc_slots][kDbAccWords]: count[kMaxKeys] u32, sum[kMaxKeys] f64
     unsigned long long wait_limit_ns;
     unsigned long long max_polls;

@@ -3,11 +3,12 @@
 //
 // SparkCL offloads each partition task through its worker's accelerator
 // (Sec. 3.1.1-3.1.3) and serialises them per device (Sec. 3.1.5).  Here one
-// kernel stays resident: the host writes a job (one partition task) and the
-// unit -> job entries of its work units into pinned host memory and then
-// advances a published-unit count (the doorbell).  Every CTA claims units in
-// order from a device counter, one ahead, waits until the doorbell covers its
-// claim, reads the job through the mapped address and runs the unit:
+// kernel stays resident.  The host writes job p (one partition task) into
+// ring slot p % job_ring of pinned host memory and then raises the count of
+// published jobs (the doorbell).  Jobs are cut into work units (streaming
+// segments or keyed pieces) numbered in publication order.  Every CTA claims
+// units from a device counter, one ahead, and waits until the units it holds
+// are available, then runs them:
 //   * a streaming segment, with the batch kernel's own segment code
 //     (stream_segment): same segment geometry, same reduction order, so a
 //     task's result is bitwise the one scl_map_reduce gives with the same
@@ -16,17 +17,20 @@
 //     into the job's count / fp64 accumulator with L2 atomics; the CTA that
 //     takes the job's last ticket writes the outputs and re-zeroes the slot.
 // The CTA that completes a job writes its result into mapped host memory and
-// then, after a system-scope fence, the job's sequence number into done[].
+// then, with a system-scope release, the job's sequence number into done[].
 //
-// Waiting: only thread 0 of a CTA waits, only for the host's doorbell, never
-// for another CTA.  One CTA at a time (a try-lock, never waited on) reads
-// the host words and mirrors them in device memory; the others read the
-// mirror and back off with __nanosleep.  Every wait ends: when the host asks
-// the kernel to stop (its claim is then unpublished and dropped), or after
-// wait_limit_ns of global-timer time or max_polls iterations, whichever comes
-// first; the CTA then sets DB_ERR_WAIT in the host's error word and returns.
-// A job descriptor that fails the bounds checks sets DB_ERR_DESC and ends the
-// CTA without touching memory through it.
+// Reads of host memory through the mapped address are slow and do not
+// overlap well across the GPU, so only one CTA at a time reads the doorbell
+// (a try-lock that nobody waits on).  When it finds new jobs it copies their
+// descriptors into device memory, writes the unit -> slot map of their units
+// with the whole CTA, and only then raises the device's count of available
+// units (release).  Every other CTA reads only device memory (acquire).
+//
+// Every wait ends: when the host asks the kernel to stop (a claim not yet
+// available is dropped), or after wait_limit_ns of global-timer time or
+// max_polls iterations, whichever comes first; the CTA then sets DB_ERR_WAIT
+// in the host's error word and returns.  A descriptor that fails a check
+// sets DB_ERR_DESC and ends the CTA without touching memory through it.
 #pragma once
 
 #include "kernels.cuh"
@@ -37,6 +41,12 @@ namespace dev {
 __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const void* p) {
     unsigned long long v;
     asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const void* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -70,51 +80,134 @@ __device__ __forceinline__ void db_set_err(const DbArgs& a, uint32_t bit) {
     st_release_sys_u32(&a.host->err, bit);
 }
 
-enum DbWait : uint32_t { DBW_READY = 0, DBW_STOP = 1, DBW_ERROR = 2 };
+enum DbAction : uint32_t { DBA_READY = 0, DBA_STOP = 1, DBA_ERROR = 2, DBA_NAP = 3, DBA_EXPAND = 4 };
 
-// Thread 0: wait until unit u is published.  Bounded (see the file comment).
-__device__ __noinline__ static uint32_t db_wait(const DbArgs& a, unsigned long long u) {
+struct DbSmem {
+    DbJob cur;                 // descriptor of the unit being run
+    unsigned long long mine;   // unit this CTA holds
+    unsigned long long x0, x1; // jobs being expanded
+    unsigned long long xend;   // units available once they are
+    uint32_t local;            // unit index within its job
+    uint32_t action;           // db_wait's decision (thread 0 writes)
+    uint32_t fetched;          // db_fetch's verdict (thread 0 writes)
+    uint32_t xok;
+};
+
+// Whole CTA, lock held: copy jobs [x0, x1) into device memory, map their
+// units, then release the units and the lock.  False (uniform): a
+// descriptor failed the continuity checks; DB_ERR_DESC is set.
+template <int BLOCK>
+__device__ __noinline__ bool db_expand(const DbArgs& a, DbSmem& db, uint32_t* scratch) {
     DbState* ds = a.state;
-    volatile unsigned long long* vtail = &ds->tail;
-    volatile uint32_t* vstop = &ds->stop;
-    const unsigned long long t0 = global_ns();
-    uint32_t nap = 32;
-    for (unsigned long long it = 0; it < a.max_polls; ++it) {
-        if (u < *vtail) {
-            __threadfence_system();
-            return DBW_READY;
+    const unsigned long long x0 = db.x0;
+    const uint32_t nj = (uint32_t)(db.x1 - x0);
+    uint4* sj = reinterpret_cast<uint4*>(scratch);   // nj * 128 bytes <= 8 KB
+    for (uint32_t i = threadIdx.x; i < nj * 8; i += BLOCK) {
+        const uint32_t slot = (uint32_t)((x0 + i / 8) % a.job_ring);
+        const uint4 v = ld_volatile_v4(reinterpret_cast<const uint4*>(a.jobs + slot) + (i % 8));
+        sj[i] = v;
+        __stcg(reinterpret_cast<uint4*>(a.djobs + slot) + (i % 8), v);
+    }
+    __syncthreads();
+    const DbJob* J = reinterpret_cast<const DbJob*>(scratch);
+    if (threadIdx.x == 0) {
+        unsigned long long u = __ldcg(&ds->tail);   // changes only under the lock
+        uint32_t ok = 1;
+        for (uint32_t i = 0; i < nj; ++i) {
+            if (J[i].ring != (uint32_t)((x0 + i) % a.job_ring) || J[i].unit0 != u ||
+                J[i].t.nseg == 0 || J[i].t.nseg > a.unit_ring)
+                ok = 0;
+            u += J[i].t.nseg;
         }
-        if (*vstop) return DBW_STOP;
-        if (atomicCAS(&ds->lock, 0u, 1u) == 0u) {
-            const unsigned long long ht = ld_acquire_sys_u64(&a.host->tail);
-            const uint32_t hs = ld_volatile_u32(&a.host->stop);
-            __threadfence();
-            if (ht > *vtail) atomicMax(&ds->tail, ht);
-            if (hs) atomicExch(&ds->stop, 1u);
+        db.xok = ok;
+        db.xend = u;
+    }
+    __syncthreads();
+    if (!db.xok) {
+        if (threadIdx.x == 0) {
+            db_set_err(a, DB_ERR_DESC);
             __threadfence();
             atomicExch(&ds->lock, 0u);
-            if (u < ht) {
-                __threadfence_system();
-                return DBW_READY;
-            }
-            if (hs) return DBW_STOP;
         }
-        if (global_ns() - t0 > a.wait_limit_ns) break;
-        __nanosleep(nap);
-        if (nap < 1024) nap <<= 1;
+        return false;
     }
-    db_set_err(a, DB_ERR_WAIT);
-    return DBW_ERROR;
+    for (uint32_t i = 0; i < nj; ++i) {
+        const uint32_t slot = J[i].ring;
+        const unsigned long long u0 = J[i].unit0;
+        for (uint32_t k = threadIdx.x; k < J[i].t.nseg; k += BLOCK)
+            __stcg(a.dunit + (u0 + k) % a.unit_ring, slot);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __stcg(&ds->jobs_seen, db.x1);
+        __threadfence();   // release: descriptors and unit map before the units
+        atomicMax(&ds->tail, db.xend);
+        __threadfence();
+        atomicExch(&ds->lock, 0u);
+    }
+    return true;
 }
 
-// Thread 0: read and check the job of unit u into `cur`.  False: bad descriptor.
-__device__ __forceinline__ static bool db_fetch(const DbArgs& a, unsigned long long u, DbJob& cur, uint32_t& local) {
-    const uint32_t j = ld_volatile_u32(a.unit_job + (u % a.unit_ring));
+// Whole CTA: wait until unit db.mine is available.  Returns DBA_READY,
+// DBA_STOP or DBA_ERROR (uniform).  Bounded (see the file comment).
+template <int BLOCK>
+__device__ __forceinline__ uint32_t db_wait(const DbArgs& a, DbSmem& db, uint32_t* scratch) {
+    DbState* ds = a.state;
+    unsigned long long t0 = 0;
+    uint32_t nap = 32;
+    if (threadIdx.x == 0) t0 = global_ns();
+    for (unsigned long long it = 0;; ++it) {
+        if (threadIdx.x == 0) {
+            uint32_t act = DBA_NAP;
+            if (db.mine < ld_acquire_gpu_u64(&ds->tail)) {
+                act = DBA_READY;
+            } else if (ld_volatile_u32(&ds->stop)) {
+                act = DBA_STOP;
+            } else if (atomicCAS(&ds->lock, 0u, 1u) == 0u) {
+                const unsigned long long hj = ld_acquire_sys_u64(&a.host->jobs);
+                const uint32_t hs = ld_volatile_u32(&a.host->stop);
+                const unsigned long long seen = __ldcg(&ds->jobs_seen);
+                if (hj > seen) {
+                    db.x0 = seen;
+                    db.x1 = hj - seen > kDbMaxExpand ? seen + kDbMaxExpand : hj;
+                    act = DBA_EXPAND;   // the lock stays held until db_expand ends
+                } else {
+                    if (hs) atomicExch(&ds->stop, 1u);
+                    __threadfence();
+                    atomicExch(&ds->lock, 0u);
+                    if (hs) act = DBA_STOP;
+                }
+            }
+            if (act == DBA_NAP && (it >= a.max_polls || global_ns() - t0 > a.wait_limit_ns)) {
+                db_set_err(a, DB_ERR_WAIT);
+                act = DBA_ERROR;
+            }
+            db.action = act;
+        }
+        __syncthreads();
+        const uint32_t act = db.action;
+        if (act == DBA_READY || act == DBA_STOP || act == DBA_ERROR) return act;
+        if (act == DBA_EXPAND) {
+            if (!db_expand<BLOCK>(a, db, scratch)) return DBA_ERROR;
+        } else if (threadIdx.x == 0) {
+            __nanosleep(nap);
+            if (nap < 512) nap <<= 1;
+        }
+        __syncthreads();   // db.action read by all before thread 0 writes it again
+    }
+}
+
+// Thread 0: the descriptor of available unit u (device memory only) into
+// `cur`, checked.  False: a bad descriptor.
+__device__ __forceinline__ static bool db_fetch(const DbArgs& a, unsigned long long u, DbJob& cur,
+                                                uint32_t& local) {
+    const uint32_t j = __ldcg(a.dunit + u % a.unit_ring);
     if (j >= a.job_ring) return false;
-    const uint4* src = reinterpret_cast<const uint4*>(a.jobs + j);
+    const uint4* src = reinterpret_cast<const uint4*>(a.djobs + j);
     uint4 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = ld_volatile_v4(src + q);
+    for (int q = 0; q < 8; ++q) v[q] = __ldcg(src + q);
     uint4* dst = reinterpret_cast<uint4*>(&cur);
 #pragma unroll
     for (int q = 0; q < 8; ++q) dst[q] = v[q];
@@ -197,12 +290,6 @@ __device__ __forceinline__ bool db_keyed_unit(const DbArgs& a, const DevTask& t,
     return threadIdx.x == 0;
 }
 
-struct DbSmem {
-    DbJob cur;
-    uint32_t local;
-    uint32_t status;
-};
-
 template <int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_doorbell(const __grid_constant__ DbArgs a) {
     __shared__ RedSmem sm;
@@ -210,20 +297,18 @@ __global__ void __launch_bounds__(BLOCK) k_doorbell(const __grid_constant__ DbAr
     extern __shared__ uint4 dyn_smem[];
     uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
 
-    unsigned long long mine = 0, ahead = 0;
-    if (threadIdx.x == 0) mine = atomicAdd(&a.state->next, 1ull);
+    unsigned long long ahead = 0;
+    if (threadIdx.x == 0) db.mine = atomicAdd(&a.state->next, 1ull);
     for (;;) {
+        __syncthreads();   // db.mine
+        if (db_wait<BLOCK>(a, db, tab) != DBA_READY) break;   // uniform
         if (threadIdx.x == 0) {
-            uint32_t st = db_wait(a, mine);
-            if (st == DBW_READY && !db_fetch(a, mine, db.cur, db.local)) {
-                db_set_err(a, DB_ERR_DESC);
-                st = DBW_ERROR;
-            }
-            db.status = st;
+            db.fetched = db_fetch(a, db.mine, db.cur, db.local) ? 1u : 0u;
+            if (db.fetched) ahead = atomicAdd(&a.state->next, 1ull);
+            else db_set_err(a, DB_ERR_DESC);
         }
         __syncthreads();
-        if (db.status != DBW_READY) break;   // uniform
-        if (threadIdx.x == 0) ahead = atomicAdd(&a.state->next, 1ull);
+        if (!db.fetched) break;   // uniform
         const DevTask t = db.cur.t;
         const uint32_t j = db.cur.ring, local = db.local;
         bool wrote;
@@ -244,12 +329,12 @@ __global__ void __launch_bounds__(BLOCK) k_doorbell(const __grid_constant__ DbAr
                 wrote = db_keyed_unit<BLOCK, IPT>(a, t, j, local, tab, sm);
                 break;
         }
-        if (wrote) {   // thread 0 of the CTA that completed the job
-            __threadfence_system();
+        if (wrote)   // thread 0 of the CTA that completed the job; the release
+                     // orders the result (this thread) and the CTA's outputs
+                     // (before the last barrier) before the done word
             st_release_sys_u32(a.done + j, db.cur.seq);
-        }
-        __syncthreads();   // db.cur and sm are free again
-        if (threadIdx.x == 0) mine = ahead;
+        __syncthreads();   // db.cur, sm and tab are free again
+        if (threadIdx.x == 0) db.mine = ahead;
     }
 }
 
