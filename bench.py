@@ -451,7 +451,32 @@ def round_trip(torch, scl, ctx) -> dict:
                                        lambda t: scl.scl_devserver_wait(ctx.handle, t))
     scl.scl_devserver_stop(ctx.handle)
     scl.scl_free_partition(ctx.handle, q)
+    out["device_polled_64x4194304_f32"] = device_polled_bulk(torch, scl, ctx)
     return out
+
+
+def device_polled_bulk(torch, scl, ctx) -> dict:
+    """Streaming bandwidth of the resident kernel: 64 fp32 poly3 jobs of
+    4,194,304 elements (1 GiB) submitted at once; makespan from the common
+    scheduled arrival to the last completion seen by the host."""
+    x = torch.randn(64 << 22, device="cuda")
+    torch.cuda.synchronize()
+    parts = [scl.scl_wrap_device(ctx.handle, x.data_ptr() + (i << 24), None, scl.SCL_F32,
+                                 1 << 22) for i in range(64)]
+    arr = scl.make_tasks([dict(part=q, kernel=scl.SCL_K_POLY3, reduce=scl.SCL_R_SUM_MIN_MAX)
+                          for q in parts])
+    alone = scl.scl_map_reduce(ctx.handle, parts[0], scl.SCL_K_POLY3, scl.SCL_R_SUM_MIN_MAX)
+    scl.scl_devserver_start(ctx.handle)
+    spans, same = [], True
+    for _ in range(8):
+        lat, res = scl.scl_devserver_replay(ctx.handle, arr, np.zeros(64), 64)
+        spans.append(float(lat.max()) / 1e6)
+        same &= float(res[0]["f64_sum"]) == alone.f64_sum
+    scl.scl_devserver_stop(ctx.handle)
+    for q in parts:
+        scl.scl_free_partition(ctx.handle, q)
+    ms = float(np.median(spans[2:]))
+    return {"makespan_ms": ms, "gbs": (1 << 30) / ms / 1e6, "result0_equals_alone": bool(same)}
 
 
 def keyed_hashed_config(torch, scl, ctx, stream, pk: float) -> dict:
