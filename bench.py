@@ -600,9 +600,9 @@ def vector_add_config(torch, scl, ctx, stream, pk: float) -> dict:
             "bytes": nbytes, "sampled_4096_bit_exact_vs_oracle": exact}
 
 
-def batch_config(torch, scl, ctx, stream) -> dict:
-    """10,000 uneven partitions: one persistent launch (graph) vs one launch each."""
-    st = stream.cuda_stream
+def build_batch(torch, scl, ctx):
+    """The 10,000-task uneven batch on the device: (specs, tasks, parts,
+    algorithmic bytes, device buffers to keep alive)."""
     specs = synth.batch_tasks()
     d = synth.batch_data_packed(specs)
     du = torch.from_numpy(d["u32"].view(np.int32)).cuda()
@@ -632,6 +632,13 @@ def batch_config(torch, scl, ctx, stream) -> dict:
                               num_keys=4096, counts_out=base, sums_out=base + 4096 * 4))
             nbytes += 8 * s.n + 4096 * 8
         parts.append(q)
+    return specs, tasks, parts, nbytes, (du, df, dk, dv, kout)
+
+
+def batch_config(torch, scl, ctx, stream) -> dict:
+    """10,000 uneven partitions: one persistent launch (graph) vs one launch each."""
+    st = stream.cuda_stream
+    specs, tasks, parts, nbytes, _bufs = build_batch(torch, scl, ctx)
     arr = scl.make_tasks(tasks)
     n = len(tasks)
     b = scl.scl_batch_create(ctx.handle, arr, n)
@@ -679,7 +686,8 @@ def batch_config(torch, scl, ctx, stream) -> dict:
 def run_ncu_case(args):
     """Small profiler cases of the other families (same kernels and sizes as
     the configs, a few launches, a 3 GiB arena): 'keyed' = 16 x 16 Mi pairs
-    keyed count+sum; 'tree' = vector-add ReduceCL of 64 x 4 Mi fp32 arrays."""
+    keyed count+sum; 'tree' = vector-add ReduceCL of 64 x 4 Mi fp32 arrays;
+    'batch' = the 10,000-task uneven batch (2.79 GB), one launch per step."""
     import torch
     from paper_1505_01120_gb300 import scl
     from paper_1505_01120_gb300.context import Context
@@ -703,6 +711,10 @@ def run_ncu_case(args):
                               num_keys=4096, counts_out=base, sums_out=base + 16384,
                               sums64_out=base + 32768))
         b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
+        fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
+    elif args.ncu_case == "batch":
+        _specs, tasks, _parts, _nb, _bufs = build_batch(torch, scl, ctx)
+        b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), len(tasks))
         fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
     else:
         k, n = 64, 1 << 22
@@ -926,7 +938,7 @@ def main():
                     help="with --ncu-case headline: run the fp32 family on the TMA "
                          "bulk-copy pipeline (256 x 4, 4 stages)")
     ap.add_argument("--ncu-case", nargs="?", const="headline", default=None,
-                    choices=["headline", "keyed", "tree"],
+                    choices=["headline", "keyed", "tree", "batch"],
                     help="profiler case: one workload's kernel only, small arena, no JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -935,7 +947,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.ncu_case in ("keyed", "tree"):
+    elif args.ncu_case in ("keyed", "tree", "batch"):
         run_ncu_case(args)
     else:
         run_ours(args, rank, world)

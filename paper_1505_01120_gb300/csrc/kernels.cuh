@@ -407,6 +407,11 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ Ke
     extern __shared__ uint4 dyn_smem[];
 
     if constexpr (mask_has_keyed(MASK)) {
+        // In the mixed kernel the keyed pieces load at most 4 vectors per thread
+        // per array: at the streaming shape's 8 they would hold 64 registers of
+        // loads and cap the kernel at 2 CTAs per SM.  Keyed results do not
+        // depend on the shape (exact counts; sums from shared-memory atomics).
+        constexpr int KIPT = (MASK == M_ALL && IPT > 4) ? 4 : IPT;
         uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
         if (a.tasks == nullptr) {
             if (is_keyed(a.single.kind) && blockIdx.x < a.nkeyed_ctas) {
@@ -414,9 +419,9 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ Ke
                 const uint64_t b = keyed_single_bound(a.single.n, blockIdx.x, G);
                 const uint64_t e = keyed_single_bound(a.single.n, blockIdx.x + 1, G);
                 if (a.single.kind == K_KEYED_MIX)
-                    keyed_piece<BLOCK, IPT, true>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
+                    keyed_piece<BLOCK, KIPT, true>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
                 else
-                    keyed_piece<BLOCK, IPT, false>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
+                    keyed_piece<BLOCK, KIPT, false>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
             }
         } else {
             const uint32_t p0 = a.kp_first[blockIdx.x], p1 = a.kp_first[blockIdx.x + 1];
@@ -424,9 +429,9 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ Ke
                 const KPiece kp = a.kpieces[p];
                 const DevTask t = a.tasks[kp.task];
                 if (t.kind == K_KEYED_MIX)
-                    keyed_piece<BLOCK, IPT, true>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, true>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
                 else
-                    keyed_piece<BLOCK, IPT, false>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, false>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
             }
         }
     }
