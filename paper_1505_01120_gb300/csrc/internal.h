@@ -27,6 +27,7 @@ constexpr uint32_t kKeyedTableWords = 2 * kMaxKeys; // count[kMaxKeys] then sum[
 constexpr uint32_t kKeyedSmemBytes = kKeyedTableWords * 4;
 constexpr uint64_t kKeyedPieceAlign = 64;           // piece boundaries, in pairs
 constexpr uint64_t kKeyedMinPiece = 32768;          // pairs; keeps table flushes cheap
+constexpr uint64_t kKeyedMinFragment = 8192;        // pairs; shorter end pieces join a neighbour
 constexpr uint64_t kKeyedTaskOverhead = 4096;       // pair-equivalents per keyed task
 constexpr uint32_t kMaxSegChunks = 4;               // a streaming segment is 1..4 chunks
 constexpr uint32_t kTargetSegsPerTask = 256;

@@ -441,6 +441,11 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
             return (uint64_t)((unsigned __int128)cta * W / Gk);
         };
         std::vector<uint32_t> cta_of_piece;
+        struct Frag {
+            uint64_t e0, e1;
+            uint32_t cta;
+        };
+        std::vector<Frag> frag;
         uint64_t A = 0;
         for (uint32_t i = 0; i < nt; ++i) {
             if (!is_keyed(kind[i])) continue;
@@ -454,20 +459,38 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
                 uint64_t e = (uint64_t)((unsigned __int128)(w - A) * t.n / cost);
                 return e / kKeyedPieceAlign * kKeyedPieceAlign;
             };
-            uint32_t slot = 0;
+            // the task's share of each CTA it spans
+            frag.clear();
             for (uint32_t cta = c0; cta < Gk && R(cta) < B; ++cta) {
                 const uint64_t lo = std::max(A, R(cta));
                 const uint64_t hi = std::min(B, cta + 1 == Gk ? W : R(cta + 1));
                 if (lo >= hi) continue;
                 const uint64_t e0 = emap(lo), e1 = emap(hi);
                 if (e0 >= e1) continue;
-                P->kpieces.push_back(KPiece{e0, e1, i, slot++});
-                cta_of_piece.push_back(cta);
+                frag.push_back(Frag{e0, e1, cta});
             }
-            if (slot == 0) {   // empty or tiny task: one (possibly empty) piece
-                P->kpieces.push_back(KPiece{0, t.n, i, 0});
-                cta_of_piece.push_back(c0);
-                slot = 1;
+            if (frag.empty()) frag.push_back(Frag{0, t.n, c0});   // empty or tiny task
+            // A small task stays whole, on the CTA that holds most of it; in a
+            // larger one, end fragments shorter than kKeyedMinFragment join
+            // their neighbour.  Fewer tasks then need the fold pass.
+            if (frag.size() > 1 && t.n <= kKeyedMinPiece) {
+                const Frag* big = &frag[0];
+                for (const Frag& f : frag)
+                    if (f.e1 - f.e0 > big->e1 - big->e0) big = &f;
+                frag = {Frag{0, t.n, big->cta}};
+            }
+            while (frag.size() > 1 && frag.front().e1 - frag.front().e0 < kKeyedMinFragment) {
+                frag[1].e0 = frag.front().e0;
+                frag.erase(frag.begin());
+            }
+            while (frag.size() > 1 && frag.back().e1 - frag.back().e0 < kKeyedMinFragment) {
+                frag[frag.size() - 2].e1 = frag.back().e1;
+                frag.pop_back();
+            }
+            uint32_t slot = 0;
+            for (const Frag& f : frag) {
+                P->kpieces.push_back(KPiece{f.e0, f.e1, i, slot++});
+                cta_of_piece.push_back(f.cta);
             }
             t.nseg = slot;
             t.slot0 = P->kslots;
