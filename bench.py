@@ -687,7 +687,10 @@ def run_ncu_case(args):
     """Small profiler cases of the other families (same kernels and sizes as
     the configs, a few launches, a 3 GiB arena): 'keyed' = 16 x 16 Mi pairs
     keyed count+sum; 'tree' = vector-add ReduceCL of 64 x 4 Mi fp32 arrays;
-    'batch' = the 10,000-task uneven batch (2.79 GB), one launch per step."""
+    'batch' = the 10,000-task uneven batch (2.79 GB), one launch per step;
+    'mix32' = 256 x 1 Mi uint32 mix32 sums in one launch; 'map' = poly3 over
+    256 Mi fp32 with the output materialised; 'large' = keyed count+sum over
+    2^20 keys, 64 Mi uniform pairs."""
     import torch
     from paper_1505_01120_gb300 import scl
     from paper_1505_01120_gb300.context import Context
@@ -716,6 +719,33 @@ def run_ncu_case(args):
         _specs, tasks, _parts, _nb, _bufs = build_batch(torch, scl, ctx)
         b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), len(tasks))
         fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
+    elif args.ncu_case == "mix32":
+        big = torch.randint(-2**31, 2**31 - 1, (256 << 20,), dtype=torch.int32, device="cuda",
+                            generator=g)
+        parts = [scl.scl_wrap_device(ctx.handle, big.data_ptr() + (i << 22), None, scl.SCL_U32,
+                                     1 << 20) for i in range(256)]
+        b = scl.scl_batch_create(ctx.handle, scl.make_tasks(
+            [dict(part=q, kernel=scl.SCL_K_MIX32, reduce=scl.SCL_R_SUM) for q in parts]), 256)
+        fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
+    elif args.ncu_case == "map":
+        n = 1 << 28
+        x = torch.randn(n, device="cuda", generator=g)
+        y = torch.empty(n, device="cuda")
+        p = scl.scl_wrap_device(ctx.handle, x.data_ptr(), None, scl.SCL_F32, n)
+        q = scl.scl_wrap_device(ctx.handle, y.data_ptr(), None, scl.SCL_F32, n)
+        fn = lambda: scl.scl_map_into(ctx.handle, p, scl.SCL_K_POLY3, q, stream=st)  # noqa: E731
+    elif args.ncu_case == "large":
+        nk, n = 1 << 20, 1 << 26
+        keys = torch.randint(0, nk, (n,), dtype=torch.int32, device="cuda", generator=g)
+        vals = torch.rand(n, device="cuda", generator=g)
+        p = scl.scl_wrap_device(ctx.handle, keys.data_ptr(), vals.data_ptr(),
+                                scl.SCL_KV_I32_F32, n)
+        dc = torch.empty(nk, dtype=torch.int32, device="cuda")
+        ds = torch.empty(nk, dtype=torch.float32, device="cuda")
+        d64 = torch.empty(nk, dtype=torch.float64, device="cuda")
+        dr = torch.empty(48, dtype=torch.uint8, device="cuda")
+        fn = lambda: scl.scl_keyed_reduce_large_async(  # noqa: E731
+            ctx.handle, p, nk, dc, ds, d64, dr, stream=st)
     else:
         k, n = 64, 1 << 22
         x = torch.randn(k * n, device="cuda", generator=g)
@@ -938,7 +968,7 @@ def main():
                     help="with --ncu-case headline: run the fp32 family on the TMA "
                          "bulk-copy pipeline (256 x 4, 4 stages)")
     ap.add_argument("--ncu-case", nargs="?", const="headline", default=None,
-                    choices=["headline", "keyed", "tree", "batch"],
+                    choices=["headline", "keyed", "tree", "batch", "mix32", "map", "large"],
                     help="profiler case: one workload's kernel only, small arena, no JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -947,7 +977,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.ncu_case in ("keyed", "tree", "batch"):
+    elif args.ncu_case in ("keyed", "tree", "batch", "mix32", "map", "large"):
         run_ncu_case(args)
     else:
         run_ours(args, rank, world)

@@ -401,8 +401,20 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
 
 // ------------------------------------------------------- persistent kernel
 
+// Residency targets, as register caps: the streaming-only kernels get a full
+// SM of threads (32 registers; the uint32 kernel's 64-bit accumulators would
+// otherwise take 40 and cost two CTAs per SM of loads in flight), kernels
+// with a keyed table half of it (64 registers; the table allows 6 CTAs, and
+// without a target ptxas takes up to 168 registers for the mixed kernel).
+// At 2 items per thread the 32-register cap would spill; those shapes get 42.
+template <int MASK, int BLOCK, int IPT>
+constexpr int persistent_min_blocks() {
+    return (MASK == M_U32 || MASK == M_F32) ? (IPT >= 4 ? 2048 : 1536) / BLOCK : 1024 / BLOCK;
+}
+
 template <int BLOCK, int IPT, int MASK>
-__global__ void __launch_bounds__(BLOCK) k_persistent(const __grid_constant__ KernelArgs a) {
+__global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT>()))
+    k_persistent(const __grid_constant__ KernelArgs a) {
     __shared__ RedSmem sm;
     extern __shared__ uint4 dyn_smem[];
 
