@@ -251,3 +251,33 @@ def test_submit_errors(env):
     finally:
         scl.scl_devserver_stop(c.handle)
     scl.scl_devserver_stop(c.handle)   # no-op when not running
+
+
+def test_small_rings_wrap_around(env):
+    """Rings far smaller than the work: 8 job slots, 64 work units (and partial
+    slots), 2 keyed accumulators.  Jobs wait for ring space, slots and unit-map
+    entries are reused many times over, and every result must still match."""
+    c, scl, st, torch, specs, data, tasks, outs, arr, alone = env
+    clear_outputs(outs)
+    torch.cuda.synchronize()
+    # jobs that fit the 64-unit ring: streaming tasks up to 64 segments, keyed
+    # tasks up to 64 pieces (the 4 Mi-element ones have 256 segments)
+    fit = [i for i, s in enumerate(specs)
+           if (s.kind == synth.KIND_KEYED and s.n <= 64 * 65536)
+           or (s.kind != synth.KIND_KEYED and s.n <= 64 * 32768 and s.n <= 1 << 21)]
+    assert len(fit) > 30
+    scl.scl_devserver_start(c.handle, job_ring=8, unit_ring=64, keyed_slots=2)
+    try:
+        for rep in range(3):
+            tickets = [(i, scl.scl_devserver_submit(c.handle, arr, i)) for i in fit]
+            for i, t in tickets:
+                check_job(scl, specs, data, outs, alone, i, scl.scl_devserver_wait(c.handle, t))
+        s = scl.scl_devserver_get_stats(c.handle)
+        assert s["ring_waits"] > 0 and s["max_inflight"] <= 8
+        assert s["completed"] == 3 * len(fit) and s["failed"] == 0 and s["device_errors"] == 0
+        # a job with more units than the ring holds is refused at once
+        big = next(i for i, sp in enumerate(specs) if sp.kind == synth.KIND_POLY3 and sp.n > 1 << 21)
+        with pytest.raises(scl.SclError):
+            scl.scl_devserver_submit(c.handle, arr, big)
+    finally:
+        scl.scl_devserver_stop(c.handle)
