@@ -12,12 +12,17 @@ Also reported on the same line:
                 peak, plus DRAM traffic per launch from the committed ncu summary
   e2e           the same metric through the C ABI from pinned HOST buffers:
                 each step loads the 64 partitions (H2D), runs the batch, reads
-                the results (D2H)
-  cpu_baseline  the CPU oracle, one thread, on the host cores
-  configs       the other workloads: mix32 on 1,048,576 uint32 (latency) and
-                on 256 x 1,048,576 (GB/s), keyed count+sum on 16 x 16,777,216
-                pairs, 10,000 uneven partitions batched vs one launch each,
-                and the continuous-batching server when built
+                the results (D2H); copies and compute are pipelined
+  cpu_baseline  the CPU oracle, one thread, on the host cores (the oracle of
+                record), plus the same call on a thread per core
+                (``all_cores``) and the host's core count and CPU model
+  configs       the other workloads: the autotuner; mix32 on 1,048,576 uint32
+                (latency) and on 256 x 1,048,576 (GB/s); keyed count+sum on
+                16 x 16,777,216 pairs, with hashed keys, and over 2^20 keys;
+                the materialised map; the vector-add ReduceCL; 10,000 uneven
+                partitions batched vs one launch each; and serving (the
+                continuous-batching server, one launch per task, and the
+                device-polling server) with p50 / p99 latency
   clocks        nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
@@ -31,6 +36,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -167,6 +173,35 @@ def cpu_oracle_poly3(host: np.ndarray, budget_s: float = 12.0):
             break
     dt = time.perf_counter() - t0
     return done * PART_N * 4 / dt / 1e9, done, dt
+
+
+def cpu_oracle_poly3_all_cores(host: np.ndarray):
+    """The same oracle call, one partition per task, on a thread per host core
+    (ctypes releases the GIL around the C call); one pass over all partitions.
+    Returns (GB/s, threads, seconds)."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.load()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda i: oracle.reduce_f32(host[i], poly=True), range(host.shape[0])))
+    dt = time.perf_counter() - t0
+    return host.shape[0] * PART_N * 4 / dt / 1e9, threads, dt
+
+
+def host_cpu() -> dict:
+    """Core count and CPU model of the host the oracle ran on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine()}
 
 
 def run_reference(args, rank: int, world: int):
@@ -963,7 +998,11 @@ def run_ours(args, rank: int, world: int):
         gbs, done, secs = cpu_oracle_poly3(hostv)
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "%d of the 64 partitions (%d MiB), one pass, 1 thread, %.1f s"
-                         % (done, done * PART_N * 4 >> 20, secs)}
+                         % (done, done * PART_N * 4 >> 20, secs), "host": host_cpu()}
+        agbs, threads, asecs = cpu_oracle_poly3_all_cores(hostv)
+        cpu["all_cores"] = {"value": agbs, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                            "sample": "the 64 partitions (1024 MiB), one pass, one partition "
+                                      "per task on %d threads, %.2f s" % (threads, asecs)}
         if not args.no_extras:
             configs = extra_configs(torch, scl, ctx, stream, pk, args.full)
 
