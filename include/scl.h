@@ -241,16 +241,21 @@ int scl_map_into(scl_ctx* ctx, scl_part in, scl_map_kernel kernel,
  * Valid (kernel, reduce, dtype): {IDENT, MIX32} x SUM on U32/I32;
  * {IDENT, POLY3} x {SUM, SUM_MIN_MAX} on F32.  (Keyed partitions: see
  * scl_keyed_reduce / scl_keyed_reduce_hashed.)  Writes *out (host) and
- * synchronises `stream`.  Integer sums are exact; fp32 sums are fp32 within
- * 64 KB segments folded in fp64 in a fixed order, so a result is bitwise
- * reproducible and identical whether the partition runs alone or in a batch
- * of the same context.  Empty partition: sums 0, min +inf, max -inf. */
+ * synchronises `stream`.  Integer sums are exact; fp32 sums are fp32 only
+ * within each thread's 4 x items_per_thread elements of a chunk and fp64
+ * after (across chunks, threads, segments), folded in a fixed order, so a
+ * result is bitwise reproducible and identical whether the partition runs
+ * alone or in a batch of the same context.  Empty partition: sums 0,
+ * min +inf, max -inf. */
 int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
                    const float coef[3], scl_reduce reduce, void* stream,
                    scl_result* out);
 
 /* The same, enqueue-only: the result is written to device memory `dev_out`
- * (one scl_result) when the stream reaches it. */
+ * (one scl_result) when the stream reaches it.  Each stream has its own
+ * scratch, so calls on different streams may overlap on the device; calls on
+ * one stream run in order.  (A destroyed stream's handle must not be reused
+ * for a new stream while its calls are still running.) */
 int scl_map_reduce_async(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
                          const float coef[3], scl_reduce reduce, void* stream,
                          scl_result* dev_out);

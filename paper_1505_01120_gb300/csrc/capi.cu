@@ -117,7 +117,6 @@ int scl_create(const scl_config* cfg, scl_ctx** out) {
                          cudaHostGetDevicePointer((void**)&c->dh_result, c->h_result, 0) !=
                              cudaSuccess))
         st = fail(SCL_E_CUDA, "cudaHostAlloc failed");
-    if (st == SCL_OK) st = ensure_scratch(c, &c->single, 1, 0, 0, kMaxKeys / kFoldBlock);
     if (st == SCL_OK && cfg->tune_cache_path) {
         c->tune_path = cfg->tune_cache_path;
         st = load_tuning(c, cfg->tune_cache_path);
@@ -368,11 +367,12 @@ static int map_reduce_common(scl_ctx* ctx, scl_part part, scl_map_kernel kernel,
 // After a synchronous single call: a non-zero device error word means a
 // bounded wait expired (or an unknown work kind was met); report it and reset
 // the single-call scratch so the next launch starts clean.
-static int check_single_error(scl_ctx* ctx) {
+static int check_single_error(scl_ctx* ctx, cudaStream_t st) {
     const uint32_t err = *reinterpret_cast<uint32_t*>(ctx->h_result + 1);
     if (!err) return SCL_OK;
-    SCL_CUDA(cudaMemset(ctx->single.hdr, 0, H_WORDS * 4));
-    SCL_CUDA(cudaMemset(ctx->single.tickets, 0, ctx->single.task_cap * 4));
+    Scratch& sc = ctx->single_for(st);
+    SCL_CUDA(cudaMemset(sc.hdr, 0, H_WORDS * 4));
+    SCL_CUDA(cudaMemset(sc.tickets, 0, sc.task_cap * 4));
     SCL_CUDA(cudaDeviceSynchronize());
     return fail((err & 4u) ? SCL_E_TIMEOUT : SCL_E_STATE,
                 "device error word 0x%x after the launch", err);
@@ -381,10 +381,10 @@ static int check_single_error(scl_ctx* ctx) {
 static int fetch_single(scl_ctx* ctx, cudaStream_t st) {
     SCL_CUDA(cudaMemcpyAsync(ctx->h_result, ctx->d_result, sizeof(scl_result),
                              cudaMemcpyDeviceToHost, st));
-    SCL_CUDA(cudaMemcpyAsync(ctx->h_result + 1, ctx->single.hdr + H_ERROR, 4,
+    SCL_CUDA(cudaMemcpyAsync(ctx->h_result + 1, ctx->single_for(st).hdr + H_ERROR, 4,
                              cudaMemcpyDeviceToHost, st));
     SCL_CUDA(cudaStreamSynchronize(st));
-    return check_single_error(ctx);
+    return check_single_error(ctx, st);
 }
 
 int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const float coef[3],
@@ -396,7 +396,7 @@ int scl_map_reduce(scl_ctx* ctx, scl_part part, scl_map_kernel kernel, const flo
     SCL_TRY(map_reduce_common(ctx, part, kernel, coef, reduce, stream, ctx->dh_result,
                               reinterpret_cast<uint32_t*>(ctx->dh_result + 1)));
     SCL_CUDA(cudaStreamSynchronize(S(stream)));
-    SCL_TRY(check_single_error(ctx));
+    SCL_TRY(check_single_error(ctx, S(stream)));
     *out = *ctx->h_result;
     return SCL_OK;
 }

@@ -337,26 +337,27 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     t.sums_out = sums;
     t.sums64_out = sums64;
     uint32_t grid;
+    Scratch& sc = c->single_for(st);
     if (is_keyed(kind)) {
         const uint32_t G = keyed_single_pieces(p.n, gmax);
         t.nseg = G;
         a.nkeyed_ctas = G;
         grid = G;
-        SCL_TRY(ensure_scratch(c, &c->single, 1, 0, G > 1 ? G : 0, kMaxKeys / kFoldBlock));
+        SCL_TRY(ensure_scratch(c, &sc, 1, 0, G > 1 ? G : 0, kMaxKeys / kFoldBlock));
     } else {
         const uint32_t chunk = (uint32_t)(sh.block * sh.ipt * 4);
         t.seg_elems = stream_seg_elems(p.n, chunk);
         t.nseg = stream_nseg(p.n, t.seg_elems);
         a.nseg_stream = t.nseg;
         grid = std::min(gmax, t.nseg);
-        SCL_TRY(ensure_scratch(c, &c->single, 1, t.nseg, 0, 0));
+        SCL_TRY(ensure_scratch(c, &sc, 1, t.nseg, 0, 0));
     }
-    a.spart = c->single.spart;
-    a.kpart = c->single.kpart;
-    a.fpart = c->single.fpart;
-    a.tickets = c->single.tickets;
-    a.task_flags = c->single.flags;
-    a.hdr = c->single.hdr;
+    a.spart = sc.spart;
+    a.kpart = sc.kpart;
+    a.fpart = sc.fpart;
+    a.tickets = sc.tickets;
+    a.task_flags = sc.flags;
+    a.hdr = sc.hdr;
     a.err_out = err_out;
     SCL_TRY(launch_entry(e, grid, a, st));
     if (is_keyed(kind) && t.nseg > 1) {

@@ -196,7 +196,10 @@ struct Ctx {
     Shape shape[M_NUM] = {Shape{256, 8, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0},
                           Shape{256, 4, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0}};
     std::map<const void*, int> occ_cache;
-    Scratch single;
+    // Scratch of single-partition launches, one per stream, so that launches
+    // on different streams may overlap on the device.
+    std::unordered_map<cudaStream_t, Scratch> single_by_stream;
+    Scratch& single_for(cudaStream_t st) { return single_by_stream[st]; }
     scl_result* d_result = nullptr;        // single-call result slot
     scl_result* h_result = nullptr;        // pinned, mapped: [0] result, [1] error word
     scl_result* dh_result = nullptr;       // device address of h_result

@@ -230,6 +230,36 @@ def test_async_result_in_device_memory(env):
     assert all(int(r["u64_sum"]) == oracle.sum_u32(a) for r in res)
 
 
+def test_async_calls_on_many_streams_overlap_safely(env):
+    """Async single-partition calls on 8 streams at once: each stream has its
+    own scratch, so overlapping launches give the same results as one at a time."""
+    c, scl, st, torch = env
+    rng = np.random.default_rng(112)
+    n = 3_000_017
+    xs = [rng.standard_normal(n, dtype=np.float32) for _ in range(8)]
+    parts = [scl.scl_load_partition(c.handle, x, scl.SCL_F32, stream=st) for x in xs]
+    alone = [scl.scl_map_reduce(c.handle, p, scl.SCL_K_POLY3, scl.SCL_R_SUM_MIN_MAX, stream=st)
+             for p in parts]
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    dev = torch.zeros(48 * 8 * 4, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    for rep in range(4):
+        for i, (p, s) in enumerate(zip(parts, streams)):
+            scl.scl_map_reduce_async(c.handle, p, scl.SCL_K_POLY3, scl.SCL_R_SUM_MIN_MAX,
+                                     dev.data_ptr() + 48 * (rep * 8 + i), stream=s.cuda_stream)
+    torch.cuda.synchronize()
+    res = dev.cpu().numpy().view(scl.RESULT_DTYPE).reshape(4, 8)
+    for rep in range(4):
+        for i in range(8):
+            r = res[rep, i]
+            assert float(r["f64_sum"]) == alone[i].f64_sum and int(r["n"]) == n, (rep, i)
+            assert float(r["f32_min"]) == alone[i].f32_min
+    for i, x in enumerate(xs):
+        check_f32_result(alone[i], x, True)
+    for p in parts:
+        scl.scl_free_partition(c.handle, p)
+
+
 def test_invalid_calls_raise(env):
     c, scl, st, _ = env
     with pytest.raises(scl.SclError) as e:
