@@ -459,12 +459,8 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys, void
 
 static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uint32_t* counts,
                               float* sums, double* sums64, scl_result* res, cudaStream_t st) {
-    if (!ctx->d_large) {
-        ctx->d_large = (uint32_t*)ctx->arena.alloc(kAlign);
-        if (!ctx->d_large) return fail(SCL_E_NOMEM, "arena: no room for scratch");
-        SCL_CUDA(cudaMemset(ctx->d_large, 0, kAlign));
-        SCL_CUDA(cudaDeviceSynchronize());
-    }
+    Scratch& sc = ctx->single_for(st);   // per stream: calls on different streams may overlap
+    SCL_TRY(ensure_scratch(ctx, &sc, 1, 0, 0, 0));
     LargeKeyedArgs a;
     memset(&a, 0, sizeof a);
     a.keys = static_cast<const char*>(p.d0);
@@ -476,8 +472,8 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
     a.sums64 = sums64;
     a.sums32 = sums;
     a.result = res;
-    a.ticket = ctx->d_large;       // reset to zero by the finishing pass
-    a.bad = ctx->d_large + 1;
+    a.ticket = sc.hdr + H_LARGE_TICKET;   // reset to zero by the finishing pass
+    a.bad = sc.hdr + H_LARGE_BAD;
     SCL_CUDA(cudaMemsetAsync(counts, 0, (size_t)nk * 4, st));
     SCL_CUDA(cudaMemsetAsync(sums64, 0, (size_t)nk * 8, st));
     SCL_CUDA(cudaMemsetAsync(res, 0, sizeof(scl_result), st));

@@ -90,7 +90,11 @@ struct alignas(16) StreamPartial {  // one streaming segment's partial
 static_assert(sizeof(StreamPartial) == 32, "StreamPartial layout");
 
 // Header words of a launch's scratch.
-enum HdrWord : uint32_t { H_QUEUE = 0, H_EXIT = 1, H_ERROR = 2, H_FOLD_EXIT = 3, H_WORDS = 16 };
+enum HdrWord : uint32_t {
+    H_QUEUE = 0, H_EXIT = 1, H_ERROR = 2, H_FOLD_EXIT = 3,
+    H_LARGE_TICKET = 8, H_LARGE_BAD = 9,   // the large-key reduce's finishing ticket and key flag
+    H_WORDS = 16
+};
 
 struct KernelArgs {
     const DevTask* tasks;       // null: single-task mode, the task is `single`

@@ -204,7 +204,6 @@ struct Ctx {
     scl_result* h_result = nullptr;        // pinned, mapped: [0] result, [1] error word
     scl_result* dh_result = nullptr;       // device address of h_result
     uint32_t* d_kout = nullptr;            // single-call keyed outputs (counts|sums|sums64)
-    uint32_t* d_large = nullptr;           // large-key reduce: ticket, bad-key flag
     std::string tune_path;
     std::unique_ptr<Server> server;
     std::unique_ptr<DevServer> devserver;

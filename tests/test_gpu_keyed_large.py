@@ -95,3 +95,35 @@ def test_large_errors(env):
         with pytest.raises(scl.SclError) as e:
             scl.scl_keyed_reduce_large(c.handle, q, nk, stream=st)
         assert e.value.status == scl.SCL_E_INVALID
+
+
+def test_large_async_on_four_streams(env):
+    """Async large-key reduces on four streams at once (per-stream scratch):
+    every table exact in counts."""
+    c, scl, st, torch = env
+    rng = np.random.default_rng(1800)
+    nk, n = 1 << 18, 3_000_001
+    data, parts = [], []
+    for _ in range(4):
+        keys = rng.integers(0, nk, size=n, dtype=np.int32)
+        vals = rng.random(n, dtype=np.float32)
+        data.append((keys, vals))
+        parts.append(scl.scl_load_partition_kv(c.handle, keys, vals, stream=st))
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = [(torch.empty(nk, dtype=torch.int32, device="cuda"),
+             torch.empty(nk, dtype=torch.float32, device="cuda"),
+             torch.empty(nk, dtype=torch.float64, device="cuda"),
+             torch.empty(48, dtype=torch.uint8, device="cuda")) for _ in range(4)]
+    for rep in range(2):
+        for p, s, o in zip(parts, streams, outs):
+            scl.scl_keyed_reduce_large_async(c.handle, p, nk, o[0], o[1], o[2], o[3],
+                                             stream=s.cuda_stream)
+        torch.cuda.synchronize()
+        for (keys, vals), o in zip(data, outs):
+            cnt = o[0].cpu().numpy().view(np.uint32)
+            assert check_keyed(cnt, o[1].cpu().numpy(), o[2].cpu().numpy(), keys, vals, nk) == 0
+            r = o[3].cpu().numpy().view(scl.RESULT_DTYPE)[0]
+            assert int(r["status"]) == 0 and int(r["u64_sum"]) == n
+    for p in parts:
+        scl.scl_free_partition(c.handle, p)
