@@ -145,6 +145,7 @@ int DevServer::start(Ctx* c, const scl_devserver_config* in) {
     for (uint32_t k = cfg.keyed_slots; k-- > 0;) free_kslots.push_back(k);
     spart.init(cfg.unit_ring);
     memset(&stats, 0, sizeof stats);
+    done.reserve(1u << 17);   // results wait here until collected: no rehash mid-trace
     stats.grid = grid;
     stats.block = (uint32_t)block;
     stats.items_per_thread = (uint32_t)ipt;
