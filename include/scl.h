@@ -13,7 +13,10 @@
  * partitions (scl_combine*).  The user kernels are a fixed catalogue of
  * hand-written sm_103a kernels (mix32, poly3, identity; sum / sum-min-max /
  * keyed count+sum).  Around it: many partitions in one persistent launch
- * (scl_batch_*), and a continuous-batching server (scl_server_*).
+ * (scl_batch_*), a continuous-batching server (scl_server_*), a
+ * device-polling server (scl_devserver_*), a launch-shape autotuner
+ * (scl_autotune) and an allocation-free single call
+ * (scl_map_reduce_noalloc).
  *
  * Conventions
  *   - Every call returns an int status: SCL_OK (0) or an SCL_E_* code.  No
@@ -22,17 +25,21 @@
  *   - Device memory: the caller hands scl_create an arena (any device buffer,
  *     e.g. a torch uint8 tensor) that it owns and keeps alive until
  *     scl_destroy.  The library sub-allocates partitions, outputs and its
- *     scratch from that arena; it calls no cudaMalloc.  It does allocate a
- *     few small pinned host staging buffers (cudaHostAlloc) at scl_create.
+ *     scratch from that arena; it calls no cudaMalloc.  It does allocate
+ *     pinned host memory (cudaHostAlloc) for result staging: a few bytes at
+ *     scl_create, and the servers' rings and staging when they start.
  *   - Streams: a `void* stream` is a cudaStream_t owned by the caller (0 =
  *     legacy default stream).  Calls named *_async only enqueue work; the
  *     others synchronise that stream before returning.
  *   - Host input pointers are read only during the call (the copy is
  *     finished before an _async call returns unless the memory is pinned, in
  *     which case it must stay untouched until the stream reaches the copy).
- *   - Thread safety: calls on one context are serialised by a context lock.
- *     Work enqueued by *_async calls of one context shares that context's
- *     scratch: keep all *_async calls of a context on one stream.
+ *   - Thread safety: calls on one context are serialised by a context lock
+ *     (the servers' submit and wait calls may come from any thread).  Work
+ *     enqueued by single-partition *_async calls uses a scratch area per
+ *     stream, so calls on different streams may overlap on the device; a
+ *     batch has its own scratch (one launch of a batch at a time);
+ *     scl_map_reduce_noalloc shares one fixed scratch (see there).
  */
 #ifndef SCL_H
 #define SCL_H
@@ -166,7 +173,7 @@ int scl_kernel_launches_total(uint64_t* out);
  * SCL_E_CUDA. */
 int scl_create(const scl_config* cfg, scl_ctx** out);
 
-/* Destroy a context: stops the server if running, frees host staging.
+/* Destroy a context: stops the servers if running, frees host staging.
  * The arena is not touched (the caller frees it). NULL is a no-op. */
 int scl_destroy(scl_ctx* ctx);
 
@@ -422,9 +429,12 @@ int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
 
 /* Plan many partition tasks as ONE persistent launch (thousands of uneven
  * partitions; the paper's "enough data" concern, Sec. 3 item 2, and kernel
- * caching per worker, Sec. 3.1.1.2).  The plan, task table and scratch are
- * placed in the arena; nothing runs yet.  Tasks keep referencing their
- * partitions: those must stay alive while the batch exists. */
+ * caching per worker, Sec. 3.1.1.2).  Streaming tasks are cut into segments
+ * that CTAs pull from a queue; keyed tasks into even shares of the keyed work
+ * on a cost-weighted share of the CTAs (the rest stream meanwhile).  The
+ * plan, task table and scratch are placed in the arena; nothing runs yet.
+ * Tasks keep referencing their partitions: those must stay alive while the
+ * batch exists.  Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED, SCL_E_NOMEM. */
 int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
                      scl_batch** out);
 
@@ -439,10 +449,12 @@ int scl_batch_launch(scl_batch* batch, void* stream);
 int scl_batch_capture(scl_batch* batch, void* stream);
 
 /* Copy the last launch's results to host results[ntasks] after synchronising
- * `stream`.  Returns SCL_E_KEY_RANGE if any task saw a bad key. */
+ * `stream`.  Returns SCL_E_KEY_RANGE if any task saw a bad key, and
+ * SCL_E_TIMEOUT / SCL_E_STATE if the launch set its device error word (the
+ * batch's scratch is then reset, so the next launch starts clean). */
 int scl_batch_results(scl_batch* batch, void* stream, scl_result* results);
 
-/* Launches of your kernels one launch of this batch makes (for accounting). */
+/* Kernel launches that one launch of this batch makes (for accounting). */
 int scl_batch_kernel_launches(scl_batch* batch, uint32_t* count);
 
 /* Free the batch (its graph and arena blocks). NULL is a no-op. */
