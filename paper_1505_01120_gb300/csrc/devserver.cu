@@ -30,36 +30,6 @@ static inline T load_acquire(const T* p) {
     return __atomic_load_n(p, __ATOMIC_ACQUIRE);
 }
 
-// ------------------------------------------------------------ RangeAlloc
-
-bool RangeAlloc::alloc(uint32_t n, uint32_t* off) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-        if (it->second < n) continue;
-        *off = it->first;
-        const uint32_t at = it->first + n, rest = it->second - n;
-        free_.erase(it);
-        if (rest) free_[at] = rest;
-        return true;
-    }
-    return false;
-}
-
-void RangeAlloc::release(uint32_t off, uint32_t n) {
-    auto next = free_.lower_bound(off);
-    if (next != free_.end() && off + n == next->first) {
-        n += next->second;
-        next = free_.erase(next);
-    }
-    if (next != free_.begin()) {
-        auto prev = std::prev(next);
-        if (prev->first + prev->second == off) {
-            prev->second += n;
-            return;
-        }
-    }
-    free_[off] = n;
-}
-
 // ------------------------------------------------------------ DevServer
 
 DevServer::~DevServer() { stop(); }

@@ -13,23 +13,10 @@
 
 #include <map>
 
+#include "range_alloc.h"
 #include "server.h"
 
 namespace scl {
-
-// First-fit allocator of index ranges [0, cap) (partial slots).
-class RangeAlloc {
-  public:
-    void init(uint32_t cap) {
-        free_.clear();
-        if (cap) free_[0] = cap;
-    }
-    bool alloc(uint32_t n, uint32_t* off);
-    void release(uint32_t off, uint32_t n);
-
-  private:
-    std::map<uint32_t, uint32_t> free_;   // offset -> length
-};
 
 struct DbInflight {
     uint64_t ticket = 0;

@@ -20,6 +20,15 @@
 
 #include "scl.h"
 
+#if !defined(__CUDACC__)   // plain C++ (the host tests): the geometry helpers below
+#ifndef __host__
+#define __host__
+#endif
+#ifndef __device__
+#define __device__
+#endif
+#endif
+
 namespace scl {
 
 constexpr uint32_t kMaxKeys = 4096;                 // shared-memory table entries

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <sstream>
 
+#include "plan_keyed.h"
 #include "runtime.h"
 
 namespace scl {
@@ -453,71 +454,29 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     P->fold_tasks.clear();
     P->kslots = 0;
     if (has_keyed) {
-        auto R = [&](uint64_t cta) -> uint64_t {
-            return (uint64_t)((unsigned __int128)cta * W / Gk);
-        };
-        std::vector<uint32_t> cta_of_piece;
-        struct Frag {
-            uint64_t e0, e1;
-            uint32_t cta;
-        };
-        std::vector<Frag> frag;
-        uint64_t A = 0;
-        for (uint32_t i = 0; i < nt; ++i) {
-            if (!is_keyed(kind[i])) continue;
+        std::vector<std::pair<uint32_t, uint64_t>> keyed;
+        for (uint32_t i = 0; i < nt; ++i)
+            if (is_keyed(kind[i])) keyed.emplace_back(i, P->tasks[i].n);
+        std::vector<KeyedPlanPiece> pieces;
+        plan_keyed_pieces(keyed, Gk, &pieces);
+        for (size_t k = 0; k < pieces.size();) {
+            const uint32_t i = pieces[k].task;
+            size_t e = k;
+            while (e < pieces.size() && pieces[e].task == i) {
+                P->kpieces.push_back(KPiece{pieces[e].e0, pieces[e].e1, i, pieces[e].slot});
+                P->kp_first[pieces[e].cta + 1]++;
+                ++e;
+            }
             DevTask& t = P->tasks[i];
-            const uint64_t cost = t.n + kKeyedTaskOverhead, B = A + cost;
-            uint32_t c0 = (uint32_t)((unsigned __int128)A * Gk / W);
-            while (c0 + 1 < Gk && R(c0 + 1) <= A) ++c0;
-            while (c0 > 0 && R(c0) > A) --c0;
-            auto emap = [&](uint64_t w) -> uint64_t {
-                if (w >= B) return t.n;
-                uint64_t e = (uint64_t)((unsigned __int128)(w - A) * t.n / cost);
-                return e / kKeyedPieceAlign * kKeyedPieceAlign;
-            };
-            // the task's share of each CTA it spans
-            frag.clear();
-            for (uint32_t cta = c0; cta < Gk && R(cta) < B; ++cta) {
-                const uint64_t lo = std::max(A, R(cta));
-                const uint64_t hi = std::min(B, cta + 1 == Gk ? W : R(cta + 1));
-                if (lo >= hi) continue;
-                const uint64_t e0 = emap(lo), e1 = emap(hi);
-                if (e0 >= e1) continue;
-                frag.push_back(Frag{e0, e1, cta});
-            }
-            if (frag.empty()) frag.push_back(Frag{0, t.n, c0});   // empty or tiny task
-            // A small task stays whole, on the CTA that holds most of it; in a
-            // larger one, end fragments shorter than kKeyedMinFragment join
-            // their neighbour.  Fewer tasks then need the fold pass.
-            if (frag.size() > 1 && t.n <= kKeyedMinPiece) {
-                const Frag* big = &frag[0];
-                for (const Frag& f : frag)
-                    if (f.e1 - f.e0 > big->e1 - big->e0) big = &f;
-                frag = {Frag{0, t.n, big->cta}};
-            }
-            while (frag.size() > 1 && frag.front().e1 - frag.front().e0 < kKeyedMinFragment) {
-                frag[1].e0 = frag.front().e0;
-                frag.erase(frag.begin());
-            }
-            while (frag.size() > 1 && frag.back().e1 - frag.back().e0 < kKeyedMinFragment) {
-                frag[frag.size() - 2].e1 = frag.back().e1;
-                frag.pop_back();
-            }
-            uint32_t slot = 0;
-            for (const Frag& f : frag) {
-                P->kpieces.push_back(KPiece{f.e0, f.e1, i, slot++});
-                cta_of_piece.push_back(f.cta);
-            }
-            t.nseg = slot;
+            t.nseg = (uint32_t)(e - k);
             t.slot0 = P->kslots;
-            if (slot > 1) {
-                P->kslots += slot;
+            if (t.nseg > 1) {
+                P->kslots += t.nseg;
                 P->fold_tasks.push_back(i);
             }
-            A = B;
+            k = e;
         }
-        // pieces were produced in non-decreasing CTA order
-        for (size_t k = 0; k < cta_of_piece.size(); ++k) P->kp_first[cta_of_piece[k] + 1]++;
+        // pieces come in non-decreasing CTA order: counts -> first piece per CTA
         for (uint32_t g = 0; g < P->grid; ++g) P->kp_first[g + 1] += P->kp_first[g];
     }
     P->fold_gridx = P->fold_tasks.empty() ? 0 : (kMaxKeys + kFoldBlock - 1) / kFoldBlock;
