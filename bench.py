@@ -18,7 +18,8 @@ Also reported on the same line:
                 (``all_cores``) and the host's core count and CPU model
   configs       the other workloads: the autotuner; mix32 on 1,048,576 uint32
                 (latency) and on 256 x 1,048,576 (GB/s); keyed count+sum on
-                16 x 16,777,216 pairs, with hashed keys, and over 2^20 keys;
+                16 x 16,777,216 pairs, on Zipf(1.2) keys, with hashed keys,
+                and over 2^20 keys (bucket-partitioned);
                 the materialised map; the vector-add ReduceCL; 10,000 uneven
                 partitions batched vs one launch each; and serving (the
                 continuous-batching server, one launch per task, and the
@@ -361,6 +362,7 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
         scl.scl_free_partition(ctx.handle, q)
     del dk, dv, outs
 
+    out["keyed_zipf_count_sum_16x4194304"] = keyed_zipf_config(torch, scl, ctx, stream, pk)
     out["keyed_hashed_count_sum_16x16777216"] = keyed_hashed_config(torch, scl, ctx, stream, pk)
     out["map_materialised_268435456"] = map_config(torch, scl, ctx, stream, pk)
     out["keyed_large_1048576_keys"] = keyed_large_config(torch, scl, ctx, stream, pk)
@@ -549,9 +551,48 @@ def keyed_hashed_config(torch, scl, ctx, stream, pk: float) -> dict:
                                                    / np.abs(osum)))}
 
 
+def keyed_zipf_config(torch, scl, ctx, stream, pk: float) -> dict:
+    """Keyed count+sum of 16 x 4,194,304 pairs over 4096 keys with Zipf(1.2)
+    frequencies (id 0 the most frequent, as in a WordCount vocabulary numbered
+    by frequency), one batched launch."""
+    import oracle
+    st = stream.cuda_stream
+    m, nk = 1 << 22, 4096
+    rng = np.random.default_rng(12)
+    keys = synth.zipf_keys_i32(16 * m, rng, nk)
+    vals = synth.unit_f32(16 * m, rng)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    outs = torch.zeros((16, nk * 4), dtype=torch.int32, device="cuda")
+    kparts, tasks = [], []
+    for i in range(16):
+        q = scl.scl_wrap_device(ctx.handle, dk.data_ptr() + i * m * 4, dv.data_ptr() + i * m * 4,
+                                scl.SCL_KV_I32_F32, m)
+        kparts.append(q)
+        base = outs[i].data_ptr()
+        tasks.append(dict(part=q, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                          num_keys=nk, counts_out=base, sums_out=base + nk * 4,
+                          sums64_out=base + nk * 8))
+    b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
+    scl.scl_batch_capture(b, st)
+    ms = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 20)
+    scl.scl_batch_results(b, 16, stream=st)
+    o0 = outs[0].cpu().numpy()
+    ocnt, osum, _ = oracle.keyed_count_sum(keys[:m], vals[:m], nk)
+    s64 = o0[2 * nk:].view(np.float64)
+    nz = ocnt > 0
+    scl.scl_batch_destroy(b)
+    for q in kparts:
+        scl.scl_free_partition(ctx.handle, q)
+    return {"gbs": 16 * m * 8 / ms / 1e6, "frac_of_hbm": 16 * m * 8 / ms / 1e6 / pk, "ms": ms,
+            "pairs_per_s": 16 * m / ms * 1e3, "id0_share": float(ocnt[0] / m),
+            "partition0_counts_exact": bool(np.array_equal(o0[:nk].view(np.uint32), ocnt)),
+            "partition0_max_rel_err": float(np.max(np.abs(s64[nz] - osum[nz]) / np.abs(osum[nz])))}
+
+
 def keyed_large_config(torch, scl, ctx, stream, pk: float) -> dict:
-    """Keyed count+sum over 2^20 keys, 64 Mi pairs: uniform keys, and Zipf(1.2)
-    keys numbered by frequency (hot ids in the shared table)."""
+    """Keyed count+sum over 2^20 keys, 64 Mi pairs (the bucket-partitioned
+    path): uniform keys, and Zipf(1.2) keys numbered by frequency."""
     import oracle
     st = stream.cuda_stream
     nk, n = 1 << 20, 1 << 26

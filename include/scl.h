@@ -119,7 +119,8 @@ typedef struct {
  *                         (NaN ignored; empty: +inf / -inf)
  *   KEYED_COUNT_SUM:      u64_sum = pairs counted, f64_sum = their value sum
  *   n:                    elements (pairs) in the partition
- *   status:               SCL_OK or SCL_E_KEY_RANGE                        */
+ *   status:               SCL_OK or SCL_E_KEY_RANGE (SCL_E_STATE: the
+ *                         large-key reduce saw its keys change)            */
 typedef struct {
     uint64_t u64_sum;
     double f64_sum;
@@ -292,15 +293,24 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
 #define SCL_MAX_LARGE_KEYS 16777216u
 
 /* The keyed reduce for key spaces larger than 4096 (a WordCount-size
- * vocabulary, Sec. 3.2.3): keys below 4096 -- the frequent ids when words
- * are numbered by frequency -- are counted in a per-block shared-memory table
- * flushed every 131,072 pairs; every other key goes straight to global
- * atomics (uint32 count, fp64 sum).  num_keys in [1, SCL_MAX_LARGE_KEYS].
- * HOST outputs of num_keys entries; sums_out is the fp64 sum rounded to fp32.
- * Counts are exact; sums agree with an fp64 fold to about 1e-7 (atomic order
- * varies between runs).  Uses temporary device tables from the arena
- * (16 B per key).  Returns SCL_E_KEY_RANGE after writing the valid pairs'
- * tables if a key was outside [0, num_keys). */
+ * vocabulary, Sec. 3.2.3).  num_keys in [1, SCL_MAX_LARGE_KEYS].  Two paths:
+ *   - bucket-partitioned, for partitions of 2^20 to 2^31 - 1 pairs whose key
+ *     and value arrays are 16-byte aligned, over more than 4096 keys: the
+ *     pairs are grouped by bucket (key / 4096) in a temporary copy, then
+ *     every bucket is counted in a per-block shared-memory table.  Needs
+ *     8 B per pair plus a few bytes per chunk and bucket from the arena;
+ *   - direct, otherwise or when the arena has no room for that copy: keys
+ *     below 4096 (the frequent ids when words are numbered by frequency) go
+ *     to a per-block shared-memory table, every other key straight to global
+ *     atomics.
+ * Both yield the same tables.  HOST outputs of num_keys entries; sums_out is
+ * the fp64 sum rounded to fp32.  Counts are exact; sums are fp32 partial sums
+ * of at most 131,072 pairs per block and key added in fp64, within 1e-5 of an
+ * fp64 fold (atomic order varies between runs).  Uses temporary device
+ * tables from the arena (16 B per key), released before returning.  Returns
+ * SCL_E_KEY_RANGE after writing the valid pairs' tables if a key was outside
+ * [0, num_keys); SCL_E_STATE if the keys changed while the call read them
+ * (the partitioned path reads them twice). */
 int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
                            uint32_t* counts_out, float* sums_out, double* sums64_out,
                            scl_result* result);
@@ -308,7 +318,9 @@ int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void*
 /* Enqueue-only form on DEVICE tables the caller owns: counts_dev (uint32),
  * sums_dev (float) and sums64_dev (double, required: it is the accumulator),
  * num_keys entries each, and dev_result (one scl_result).  All are zeroed or
- * overwritten on `stream` before use. */
+ * overwritten on `stream` before use.  The partitioned path's temporary copy
+ * is kept per stream (reused by later calls on that stream, returned by
+ * scl_destroy); growing it synchronises the device. */
 int scl_keyed_reduce_large_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,
                                  void* stream, uint32_t* counts_dev, float* sums_dev,
                                  double* sums64_dev, scl_result* dev_result);

@@ -8,6 +8,7 @@
 
 #include "runtime.h"
 #include "devserver.h"
+#include "radix.h"
 #include "server.h"
 
 namespace scl {
@@ -457,8 +458,90 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys, void
     return SCL_OK;
 }
 
+// Bucket tables of the partitioned path: per call (stored in *call_tmp; the
+// caller releases it after synchronising) or kept per stream and grown on
+// demand.  Null when the arena has no room.
+static void* radix_tables(Ctx* c, Scratch& sc, size_t bytes, void** call_tmp) {
+    if (call_tmp) return *call_tmp = c->arena.alloc(bytes);
+    if (sc.radix && sc.radix_cap >= bytes) return sc.radix;
+    if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;   // earlier calls may read it
+    if (sc.radix) {
+        sc.blocks.erase(std::remove(sc.blocks.begin(), sc.blocks.end(), sc.radix), sc.blocks.end());
+        c->arena.release(sc.radix);
+        sc.radix = nullptr;
+        sc.radix_cap = 0;
+    }
+    size_t cap = align_up(bytes + bytes / 8);
+    void* q = c->arena.alloc(cap);
+    if (!q) q = c->arena.alloc(cap = bytes);
+    if (!q) return nullptr;
+    sc.radix = q;
+    sc.radix_cap = cap;
+    sc.blocks.push_back(q);
+    return q;
+}
+
+// Histogram, scan, scatter and per-bucket reduce (radix.h).  *launched is
+// false, with nothing enqueued, when the arena has no room for the tables.
+static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, uint32_t* counts,
+                        double* sums64, uint32_t* bad, cudaStream_t st, void** call_tmp,
+                        bool* launched) {
+    *launched = false;
+    const uint32_t nb = (nk + kMaxKeys - 1) / kMaxKeys;
+    const void* scatter = radix_scatter_fn(radix_staged(nb));
+    const size_t hist_smem = (size_t)nb * 4, scat_smem = radix_scatter_smem(nb);   // < 48 KB
+    int occ_h = 0, occ_s = 0, occ_r = 0;
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, radix_hist_fn(), kRadixBlock,
+                                                           hist_smem));
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, scatter, kRadixBlock,
+                                                           scat_smem));
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, radix_reduce_fn(), kRadixBlock,
+                                                           0));
+    const uint32_t slots_h = (uint32_t)c->sms * std::max(occ_h, 1);
+    const uint32_t slots_s = (uint32_t)c->sms * std::max(occ_s, 1);
+    const uint32_t slots_r = (uint32_t)c->sms * std::max(occ_r, 1);
+    const RadixGeometry g = radix_geometry(p.n, nk, slots_s);
+    const RadixLayout l = radix_layout(p.n, g);
+    char* t = static_cast<char*>(radix_tables(c, sc, l.total, call_tmp));
+    if (!t) return SCL_OK;
+    RadixArgs r;
+    memset(&r, 0, sizeof r);
+    r.keys = static_cast<const char*>(p.d0);
+    r.vals = static_cast<const char*>(p.d1);
+    r.n = p.n;
+    r.num_keys = nk;
+    r.nb = g.nb;
+    r.chunk = g.chunk;
+    r.nchunks = g.nchunks;
+    r.bk = reinterpret_cast<uint32_t*>(t + l.bk);
+    r.hist = reinterpret_cast<uint32_t*>(t + l.hist);
+    r.tot = reinterpret_cast<uint32_t*>(t + l.tot);
+    r.bstart = reinterpret_cast<uint32_t*>(t + l.bstart);
+    r.counts = counts;
+    r.sums64 = sums64;
+    r.ticket = sc.hdr + H_RADIX_TICKET;   // reset to zero by the scan's last CTA
+    r.bad = bad;
+    void* params[] = {&r};
+    SCL_CUDA(cudaLaunchKernel(radix_hist_fn(), dim3(std::min(g.nchunks, slots_h)),
+                              dim3(kRadixBlock), params, hist_smem, st));
+    const uint32_t rows = kRadixScanBlock / 32;   // one warp per bucket row
+    SCL_CUDA(cudaLaunchKernel(radix_scan_fn(), dim3((g.nb + rows - 1) / rows),
+                              dim3(kRadixScanBlock), params, 0, st));
+    SCL_CUDA(cudaLaunchKernel(scatter, dim3(std::min(g.nchunks, slots_s)), dim3(kRadixBlock),
+                              params, scat_smem, st));
+    SCL_CUDA(cudaLaunchKernel(radix_reduce_fn(), dim3(slots_r), dim3(kRadixBlock), params, 0, st));
+    count_launches(4);
+    *launched = true;
+    return SCL_OK;
+}
+
+// Large key spaces: the bucket-partitioned path for partitions of at least
+// kRadixMinPairs aligned pairs over more than kMaxKeys keys, when its tables
+// fit the arena; otherwise the direct kernel (shared table for ids below
+// kMaxKeys, global atomics for the rest).  Then the finishing pass.
 static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uint32_t* counts,
-                              float* sums, double* sums64, scl_result* res, cudaStream_t st) {
+                              float* sums, double* sums64, scl_result* res, cudaStream_t st,
+                              void** call_tmp) {
     Scratch& sc = ctx->single_for(st);   // per stream: calls on different streams may overlap
     SCL_TRY(ensure_scratch(ctx, &sc, 1, 0, 0, 0));
     LargeKeyedArgs a;
@@ -479,7 +562,10 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
     SCL_CUDA(cudaMemsetAsync(res, 0, sizeof(scl_result), st));
     SCL_CUDA(cudaMemsetAsync(a.bad, 0, 4, st));
     void* params[] = {&a};
-    if (p.n) {
+    bool done = false;
+    if (a.aligned && nk > kMaxKeys && p.n >= kRadixMinPairs && p.n <= kRadixMaxPairs)
+        SCL_TRY(launch_radix(ctx, sc, p, nk, counts, sums64, a.bad, st, call_tmp, &done));
+    if (p.n && !done) {
         const void* fn = large_keyed_kernel_fn(a.aligned);
         int nb = 0;
         SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0));
@@ -515,7 +601,7 @@ int scl_keyed_reduce_large_async(scl_ctx* ctx, scl_part part, uint32_t num_keys,
     if (!counts_dev || !sums_dev || !sums64_dev || !dev_result)
         return fail(SCL_E_INVALID, "all device tables and the result are required");
     return launch_large_keyed(ctx, *p, num_keys, counts_dev, sums_dev, sums64_dev, dev_result,
-                              S(stream));
+                              S(stream), nullptr);
 }
 
 int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
@@ -532,7 +618,8 @@ int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void*
     uint32_t* dc = (uint32_t*)(buf + nk * 8);
     float* ds = (float*)(buf + nk * 12);
     scl_result* dr = (scl_result*)(buf + align_up(nk * 16));
-    int st = launch_large_keyed(ctx, *p, num_keys, dc, ds, d64, dr, S(stream));
+    void* tmp = nullptr;   // bucket tables of the partitioned path, if it runs
+    int st = launch_large_keyed(ctx, *p, num_keys, dc, ds, d64, dr, S(stream), &tmp);
     if (st == SCL_OK) {
         cudaStream_t s = S(stream);
         if (cudaMemcpyAsync(counts_out, dc, nk * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -546,8 +633,11 @@ int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void*
     }
     cudaStreamSynchronize(S(stream));
     ctx->arena.release(buf);
+    if (tmp) ctx->arena.release(tmp);
     if (st != SCL_OK) return st;
     if (result) *result = *ctx->h_result;
+    if (ctx->h_result->status == SCL_E_STATE)
+        return fail(SCL_E_STATE, "the keys changed while the call read them");
     if (ctx->h_result->status == SCL_E_KEY_RANGE)
         return fail(SCL_E_KEY_RANGE, "a key outside [0, %u) was skipped", num_keys);
     return SCL_OK;

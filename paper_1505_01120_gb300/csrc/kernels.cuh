@@ -291,32 +291,44 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
 
 // ------------------------------------------------------------ keyed piece
 
+// Counts go straight to the table (integer adds to one address do not
+// serialise); fp32 sums of ids below kKeyedHead go to this thread's head copy
+// (`head`), the rest to the table.  Hashed ids spread the frequent keys, so
+// the hashed form uses the table only.
 template <bool HASHED>
 __device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, uint32_t* cnt,
-                                          float* sum, uint32_t& bad) {
+                                          float* sum, float* head, uint32_t& bad) {
     if constexpr (HASHED) k = __umulhi(mix32(k), nk);   // (mix32(key) * nk) >> 32, always < nk
     if (k < nk) {           // a negative int32 key is a huge uint32: rejected here
         atomicAdd(&cnt[k], 1u);
-        atomicAdd(&sum[k], __uint_as_float(v));
+        atomicAdd(!HASHED && k < kKeyedHead ? &head[k] : &sum[k], __uint_as_float(v));
     } else {
         bad = 1u;
     }
 }
 
 // Pairs [b, e) of a keyed task accumulated into the CTA's shared-memory table
-// (count[kMaxKeys] then fp32 sum[kMaxKeys]), zeroed first.  Returns, in every
-// thread, whether any key was out of range.  Ends with a barrier.
+// (count[kMaxKeys] then fp32 sum[kMaxKeys], then the head copies), zeroed
+// first; the head copies are folded into the table at the end.  Returns, in
+// every thread, whether any key was out of range.  Ends with a barrier.
 template <int BLOCK, int IPT, bool HASHED>
 __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, uint64_t e,
                                                 uint32_t* tab) {
     constexpr uint32_t CH = BLOCK * IPT * 4;
+    constexpr uint32_t NCOPY = BLOCK / 32 * kKeyedHeadClasses;
+    static_assert(kKeyedHeadWords(BLOCK) * 4 + kKeyedTableWords * 4 <= kKeyedSmemBytes, "smem");
     uint32_t* cnt = tab;
     float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
+    float* heads = reinterpret_cast<float*>(tab + kKeyedTableWords);
+    float* head = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
+                           (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
     const uint32_t nk = t.num_keys;
     for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
         cnt[k] = 0u;
         sum[k] = 0.f;
     }
+    if (!HASHED)
+        for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(BLOCK); i += BLOCK) heads[i] = 0.f;
     __syncthreads();
 
     const char* kb = static_cast<const char*>(t.in0);
@@ -333,10 +345,10 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
             for (int j = 0; j < IPT; ++j) vv[j] = ld_stream_v4(vb + off + (size_t)j * BLOCK * 16);
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                keyed_add<HASHED>(kv[j].x, vv[j].x, nk, cnt, sum, bad);
-                keyed_add<HASHED>(kv[j].y, vv[j].y, nk, cnt, sum, bad);
-                keyed_add<HASHED>(kv[j].z, vv[j].z, nk, cnt, sum, bad);
-                keyed_add<HASHED>(kv[j].w, vv[j].w, nk, cnt, sum, bad);
+                keyed_add<HASHED>(kv[j].x, vv[j].x, nk, cnt, sum, head, bad);
+                keyed_add<HASHED>(kv[j].y, vv[j].y, nk, cnt, sum, head, bad);
+                keyed_add<HASHED>(kv[j].z, vv[j].z, nk, cnt, sum, head, bad);
+                keyed_add<HASHED>(kv[j].w, vv[j].w, nk, cnt, sum, head, bad);
             }
         }
     }
@@ -348,10 +360,19 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
             for (int q = 0; q < 4; ++q)
                 if (g + q < e)
                     keyed_add<HASHED>(ld_stream_b32(kb + (g + q) * 4),
-                                      ld_stream_b32(vb + (g + q) * 4), nk, cnt, sum, bad);
+                                      ld_stream_b32(vb + (g + q) * 4), nk, cnt, sum, head, bad);
         }
     }
-    return __syncthreads_or((int)bad);
+    const int any_bad = __syncthreads_or((int)bad);
+    if (!HASHED) {
+        for (uint32_t k = threadIdx.x; k < min(nk, kKeyedHead); k += BLOCK) {
+            float h = 0.f;
+            for (uint32_t r = 0; r < NCOPY; ++r) h += heads[r * kKeyedHeadStride + k];
+            sum[k] += h;
+        }
+        __syncthreads();
+    }
+    return any_bad;
 }
 
 // One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
@@ -705,13 +726,13 @@ __global__ void __launch_bounds__(256) k_tree_add(const __grid_constant__ TreeAr
 // ------------------------------------------------- large key spaces
 
 __device__ __forceinline__ void large_add(uint32_t k, uint32_t vbits, const LargeKeyedArgs& a,
-                                          uint32_t* hc, float* hs, uint32_t& bad) {
+                                          uint32_t* hc, float* hs, float* head, uint32_t& bad) {
     const float v = __uint_as_float(vbits);
     if (k >= a.num_keys) {
         bad = 1u;
     } else if (k < kMaxKeys) {
         atomicAdd(&hc[k], 1u);
-        atomicAdd(&hs[k], v);
+        atomicAdd(k < kKeyedHead ? &head[k] : &hs[k], v);
     } else {
         atomicAdd(&a.counts[k], 1u);
         atomicAdd(&a.sums64[k], (double)v);
@@ -719,11 +740,16 @@ __device__ __forceinline__ void large_add(uint32_t k, uint32_t vbits, const Larg
 }
 
 // Grid-stride over pieces of kLargePiece pairs; each piece zeroes the shared
-// hot table, accumulates, and flushes its non-zero entries to global memory.
+// hot table (and the head copies of its first ids), accumulates, and flushes
+// its non-zero entries to global memory.
 template <bool ALIGNED>
 __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ LargeKeyedArgs a) {
+    constexpr uint32_t NCOPY = 256 / 32 * kKeyedHeadClasses;
     __shared__ uint32_t hc[kMaxKeys];
     __shared__ float hs[kMaxKeys];
+    __shared__ float heads[kKeyedHeadWords(256)];
+    float* head = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
+                           (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
     const uint32_t hot = min(a.num_keys, kMaxKeys);
     const uint64_t npieces = (a.n + kLargePiece - 1) / kLargePiece;
     uint32_t bad = 0;
@@ -732,6 +758,7 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
             hc[i] = 0u;
             hs[i] = 0.f;
         }
+        for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(256); i += blockDim.x) heads[i] = 0.f;
         __syncthreads();
         const uint64_t b = pc * kLargePiece;
         const uint64_t e = min(b + kLargePiece, a.n);
@@ -747,21 +774,25 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
                 for (int j = 0; j < 4; ++j) vv[j] = ld_stream_v4(a.vals + off + (size_t)j * 4096);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    large_add(kv[j].x, vv[j].x, a, hc, hs, bad);
-                    large_add(kv[j].y, vv[j].y, a, hc, hs, bad);
-                    large_add(kv[j].z, vv[j].z, a, hc, hs, bad);
-                    large_add(kv[j].w, vv[j].w, a, hc, hs, bad);
+                    large_add(kv[j].x, vv[j].x, a, hc, hs, head, bad);
+                    large_add(kv[j].y, vv[j].y, a, hc, hs, head, bad);
+                    large_add(kv[j].z, vv[j].z, a, hc, hs, head, bad);
+                    large_add(kv[j].w, vv[j].w, a, hc, hs, head, bad);
                 }
             }
         }
         for (uint64_t g = i + threadIdx.x; g < e; g += blockDim.x)
-            large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, hc, hs, bad);
+            large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, hc, hs,
+                      head, bad);
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < hot; k += blockDim.x) {
             const uint32_t c = hc[k];
             if (c) {
+                float t = hs[k];
+                if (k < kKeyedHead)
+                    for (uint32_t r = 0; r < NCOPY; ++r) t += heads[r * kKeyedHeadStride + k];
                 atomicAdd(&a.counts[k], c);
-                atomicAdd(&a.sums64[k], (double)hs[k]);
+                atomicAdd(&a.sums64[k], (double)t);
             }
         }
         __syncthreads();   // the table is zeroed again by the next piece
@@ -798,7 +829,10 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
             r->f32_sum = (float)tot;
             r->f32_min = CUDART_INF_F;
             r->f32_max = -CUDART_INF_F;
-            r->status = __ldcg(a.bad) ? SCL_E_KEY_RANGE : SCL_OK;
+            // bit 0: a key out of range; bit 1: the bucket-partitioned path
+            // counted the keys differently in its two reads (they changed)
+            const uint32_t bad = __ldcg(a.bad);
+            r->status = (bad & 2u) ? SCL_E_STATE : bad ? SCL_E_KEY_RANGE : SCL_OK;
             r->n = a.n;
             r->kind = K_KEYED;
             *a.ticket = 0u;

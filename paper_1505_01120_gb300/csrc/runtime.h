@@ -108,6 +108,8 @@ struct Scratch {
     size_t kpart_cap = 0;
     StreamPartial* fpart = nullptr;
     size_t fpart_cap = 0;
+    void* radix = nullptr;          // the large-key reduce's bucket tables (async calls)
+    size_t radix_cap = 0;
     std::vector<void*> blocks;
 };
 

@@ -5,16 +5,22 @@
 //   * the batch planner's keyed pieces cover every keyed task exactly once,
 //     in task order with non-decreasing CTAs, small tasks whole, no short end
 //     fragments, CTAs in range;
-//   * the range allocator against a reference bitmap under random use.
+//   * the range allocator against a reference bitmap under random use;
+//   * the bucket-partitioned large-key reduce: its geometry and table layout,
+//     and, replaying the four passes' offset arithmetic on random keys, that
+//     every kept pair is written once inside its bucket and read once by
+//     the reduce's CTA shares, with no index outside the tables.
 // Prints "ok" and exits 0, or names the first failed check and exits 1.
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <random>
 #include <vector>
 
 #include "internal.h"
 #include "plan_keyed.h"
+#include "radix.h"
 #include "range_alloc.h"
 
 using namespace scl;
@@ -165,11 +171,135 @@ static void check_range_alloc() {
     }
 }
 
+static void check_radix() {
+    std::mt19937_64 rng(5);
+    // geometry and layout over a wide range of sizes
+    for (int it = 0; it < 20000; ++it) {
+        const uint64_t n = kRadixMinPairs + rng() % (kRadixMaxPairs - kRadixMinPairs + 1);
+        const uint32_t nk = kMaxKeys + 1 + (uint32_t)(rng() % (kMaxLargeKeys - kMaxKeys));
+        const uint32_t slots = 1 + (uint32_t)(rng() % 4096);
+        const RadixGeometry g = radix_geometry(n, nk, slots);
+        CHECK(g.chunk % kRadixChunkAlign == 0 && g.chunk >= kRadixChunkAlign, "chunk %u", g.chunk);
+        CHECK((uint64_t)g.nchunks * g.chunk >= n && (uint64_t)(g.nchunks - 1) * g.chunk < n,
+              "chunks do not cover n %llu", (unsigned long long)n);
+        CHECK(g.nb >= 2 && (uint64_t)g.nb * kMaxKeys >= nk && (uint64_t)(g.nb - 1) * kMaxKeys < nk,
+              "buckets %u for %u keys", g.nb, nk);
+        CHECK(g.nchunks <= 2ull * slots + 1 || g.chunk == kRadixChunkAlign, "too many chunks");
+        const RadixLayout l = radix_layout(n, g);
+        CHECK(l.hist >= n * 8 + 8 || (n % 2 == 0 && l.hist >= n * 8),
+              "no room for the last 16-byte load");
+        CHECK(l.hist % 256 == 0 && l.tot % 256 == 0 && l.bstart % 256 == 0, "unaligned table");
+        CHECK(l.tot >= l.hist + (uint64_t)g.nb * g.nchunks * 4 && l.bstart >= l.tot + g.nb * 4ull &&
+                  l.total >= l.bstart + (g.nb + 1ull) * 4,
+              "tables overlap");
+        CHECK(radix_scatter_smem(g.nb) <= 227 * 1024, "scatter shared memory %u",
+              radix_scatter_smem(g.nb));
+    }
+    // replay of the passes' offsets (scaled-down sizes, same formulas)
+    for (int it = 0; it < 40; ++it) {
+        const uint64_t n = kRadixMinPairs + rng() % (3 * kRadixMinPairs);
+        const uint32_t shape = it % 4;
+        const uint32_t nk = shape == 0 ? kMaxKeys + 1 + (uint32_t)(rng() % 10)
+                                       : kMaxKeys * (2 + (uint32_t)(rng() % 300)) - (uint32_t)(rng() % 7);
+        const uint32_t slots = 64 + (uint32_t)(rng() % 800), grid4 = 64 + (uint32_t)(rng() % 800);
+        const RadixGeometry g = radix_geometry(n, nk, slots);
+        std::vector<uint32_t> keys(n);
+        for (auto& k : keys) {
+            k = shape == 1 ? (uint32_t)(rng() % 3)                  // one bucket
+                : shape == 2 ? nk - 1 - (uint32_t)(rng() % 2)      // the last bucket
+                             : (uint32_t)(rng() % (nk + nk / 50)); // some out of range
+        }
+        if (shape == 3) std::sort(keys.begin(), keys.end());
+        // pass 1 + scan
+        std::vector<uint32_t> hist((size_t)g.nb * g.nchunks, 0), bstart(g.nb + 1, 0);
+        for (uint32_t c = 0; c < g.nchunks; ++c)
+            for (uint64_t i = (uint64_t)c * g.chunk; i < std::min<uint64_t>(n, (uint64_t)(c + 1) * g.chunk); ++i)
+                if (keys[i] < nk) ++hist[(size_t)(keys[i] / kMaxKeys) * g.nchunks + c];
+        for (uint32_t b = 0; b < g.nb; ++b) {
+            uint32_t run = 0;
+            for (uint32_t c = 0; c < g.nchunks; ++c) {
+                const uint32_t v = hist[(size_t)b * g.nchunks + c];
+                hist[(size_t)b * g.nchunks + c] = run;
+                run += v;
+            }
+            bstart[b + 1] = bstart[b] + run;
+        }
+        const uint64_t nv = bstart[g.nb];
+        // pass 3: each chunk's tiles advance per-bucket cursors
+        std::vector<uint32_t> owner(nv, UINT32_MAX);
+        for (uint32_t c = 0; c < g.nchunks; ++c) {
+            std::vector<uint32_t> cur(g.nb);
+            for (uint32_t b = 0; b < g.nb; ++b) cur[b] = bstart[b] + hist[(size_t)b * g.nchunks + c];
+            const uint64_t e0 = std::min<uint64_t>(n, (uint64_t)(c + 1) * g.chunk);
+            for (uint64_t t0 = (uint64_t)c * g.chunk; t0 < e0; t0 += kRadixTile) {
+                uint32_t tn = 0;
+                for (uint64_t i = t0; i < std::min<uint64_t>(e0, t0 + kRadixTile); ++i) {
+                    if (keys[i] >= nk) continue;
+                    ++tn;
+                    const uint32_t b = keys[i] / kMaxKeys;
+                    const uint64_t pos = cur[b]++;
+                    CHECK(pos >= bstart[b] && pos < bstart[b + 1], "pair %llu outside its bucket",
+                          (unsigned long long)i);
+                    CHECK(owner[pos] == UINT32_MAX, "position %llu written twice",
+                          (unsigned long long)pos);
+                    owner[pos] = keys[i];
+                }
+                CHECK(tn <= kRadixTile, "tile overflow");
+            }
+        }
+        for (uint64_t q = 0; q < nv; ++q) CHECK(owner[q] != UINT32_MAX, "position %llu unwritten",
+                                                (unsigned long long)q);
+        // pass 4: even CTA shares, bucket search, pieces of at most kLargePiece
+        std::vector<uint32_t> cnt(nk, 0), seen(nv, 0);
+        for (uint32_t blk = 0; blk < grid4; ++blk) {
+            const uint64_t lo = nv * blk / grid4, hi = nv * (blk + 1) / grid4;
+            if (lo >= hi) continue;
+            uint32_t bl = 0, bh = g.nb - 1;
+            while (bl < bh) {
+                const uint32_t mid = (bl + bh + 1) / 2;
+                if (bstart[mid] <= lo) bl = mid;
+                else bh = mid - 1;
+            }
+            CHECK(bstart[bl] <= lo && lo < bstart[bl + 1], "search missed pair %llu",
+                  (unsigned long long)lo);
+            uint64_t s = lo;
+            for (uint32_t b = bl; s < hi && b < g.nb; ++b) {
+                const uint64_t bend = std::min<uint64_t>(bstart[b + 1], nv);
+                if (bend <= s) continue;
+                const uint64_t se = std::min(hi, bend);
+                const uint32_t hot = std::min(kMaxKeys, nk - b * kMaxKeys);
+                for (uint64_t p0 = s; p0 < se; p0 += kLargePiece) {
+                    const uint64_t p1 = std::min(p0 + kLargePiece, se);
+                    // 16-byte loads of two pairs: words [4 q, 4 q + 4)
+                    const uint64_t q0 = p0 >> 1, q1 = (p1 + 1) >> 1;
+                    CHECK((q1 - 1) * 16 + 16 <= radix_layout(n, g).hist, "load past bk");
+                    for (uint64_t i = p0; i < p1; ++i) {
+                        const uint32_t k = owner[i];
+                        CHECK(k / kMaxKeys == b && k % kMaxKeys < hot, "pair %llu in bucket %u",
+                              (unsigned long long)i, b);
+                        ++seen[i];
+                        ++cnt[k];
+                    }
+                    (void)q0;
+                }
+                s = se;
+            }
+        }
+        for (uint64_t q = 0; q < nv; ++q) CHECK(seen[q] == 1, "pair %llu reduced %u times",
+                                                (unsigned long long)q, seen[q]);
+        std::vector<uint32_t> ref(nk, 0);
+        for (uint32_t k : keys)
+            if (k < nk) ++ref[k];
+        CHECK(cnt == ref, "counts differ");
+    }
+}
+
 int main() {
     check_stream_segments();
     if (!g_fail) check_keyed_single();
     if (!g_fail) check_keyed_plan();
     if (!g_fail) check_range_alloc();
+    if (!g_fail) check_radix();
     if (g_fail) return 1;
     printf("ok\n");
     return 0;

@@ -127,3 +127,120 @@ def test_large_async_on_four_streams(env):
             assert int(r["status"]) == 0 and int(r["u64_sum"]) == n
     for p in parts:
         scl.scl_free_partition(c.handle, p)
+
+
+def _launches(scl, fn):
+    before = scl.scl_kernel_launches_total()
+    out = fn()
+    return out, scl.scl_kernel_launches_total() - before
+
+
+# Bucket-partitioned path (partitions of at least 2^20 aligned pairs over more
+# than 4096 keys): histogram, scan, scatter and per-bucket reduce kernels,
+# then the finishing pass -- 5 launches; the direct path makes 2.
+RADIX_CASES = {
+    # one key for every pair: a single bucket split over the whole grid
+    "one_key": lambda rng: (1 << 20, np.full((1 << 20) + 3, 777_777, np.int32)),
+    # only the last, partial bucket (3 keys) is used
+    "last_bucket": lambda rng: (4096 * 5 + 3,
+                                rng.integers(4096 * 5, 4096 * 5 + 3, (1 << 20) + 1,
+                                             dtype=np.int32)),
+    # odd length: ragged tails in every pass
+    "odd_length": lambda rng: (1 << 20, rng.integers(0, 1 << 20, (1 << 20) + 12_345,
+                                                    dtype=np.int32)),
+    # 4096 buckets, most of them holding a few hundred pairs
+    "max_buckets": lambda rng: (1 << 24, rng.integers(0, 1 << 24, 1 << 21, dtype=np.int32)),
+    # sorted keys: CTAs that hold whole buckets store them without atomics
+    "sorted": lambda rng: (1 << 22, np.sort(rng.integers(0, 1 << 22, 1 << 21,
+                                                         dtype=np.int32))),
+    # Zipf(1.2): most pairs in bucket 0, one hot key per warp
+    "zipf": lambda rng: (1 << 20, synth.zipf_keys_i32(3_000_000, rng, 1 << 20)),
+    # two keys in different buckets, alternating
+    "two_buckets": lambda rng: (8192 + 10, np.tile(np.array([3, 8195], np.int32),
+                                                   (1 << 20) // 2 + 7)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RADIX_CASES))
+def test_large_radix_cases(env, case):
+    c, scl, st, _ = env
+    rng = np.random.default_rng(1900 + len(case))
+    nk, keys = RADIX_CASES[case](rng)
+    vals = rng.random(keys.size, dtype=np.float32)
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    (cnt, sums, s64, r), nl = _launches(
+        scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
+    assert nl == 5
+    assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+    assert r.status == 0 and r.u64_sum == keys.size and r.n == keys.size
+    scl.scl_free_partition(c.handle, p)
+
+
+def test_large_radix_out_of_range(env):
+    """Out-of-range keys are dropped by the histogram and the scatter alike;
+    the tables of the valid pairs stay exact."""
+    c, scl, st, _ = env
+    rng = np.random.default_rng(2000)
+    nk, n = 300_000, (1 << 20) + 77
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    keys[[0, 1, 4096, n // 2, n - 1]] = [nk, -1, 1 << 30, nk + 4096, -(1 << 31)]
+    vals = rng.random(n, dtype=np.float32)
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    with pytest.raises(scl.SclError) as e:
+        scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st)
+    assert e.value.status == scl.SCL_E_KEY_RANGE
+    cnt, sums, s64, r = e.value.tables
+    assert check_keyed(cnt, sums, s64, keys, vals, nk) == 5
+    assert r.u64_sum == n - 5
+    scl.scl_free_partition(c.handle, p)
+
+
+def test_large_radix_and_direct_agree(env):
+    """The same pairs through the partitioned path (aligned) and the direct
+    kernel (a view one pair in, so 4-byte aligned only): counts identical,
+    sums within the fp32 tolerance of the oracle on both."""
+    c, scl, st, torch = env
+    rng = np.random.default_rng(2100)
+    nk, n = 1 << 19, (1 << 21) + 1
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    vals = rng.random(n, dtype=np.float32)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    torch.cuda.synchronize()
+    whole = scl.scl_wrap_device(c.handle, dk.data_ptr(), dv.data_ptr(), scl.SCL_KV_I32_F32, n)
+    tail = scl.scl_wrap_device(c.handle, dk.data_ptr() + 4, dv.data_ptr() + 4,
+                               scl.SCL_KV_I32_F32, n - 1)
+    (a, _, _, _), na = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, whole, nk,
+                                                                        stream=st))
+    (b, bs, b64, _), nb_ = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, tail, nk,
+                                                                            stream=st))
+    assert (na, nb_) == (5, 2)
+    ref = np.bincount(keys, minlength=nk).astype(np.uint32)
+    assert np.array_equal(a, ref)
+    ref[keys[0]] -= 1
+    assert np.array_equal(b, ref)
+    assert check_keyed(b, bs, b64, keys[1:], vals[1:], nk) == 0
+    scl.scl_free_partition(c.handle, whole)
+    scl.scl_free_partition(c.handle, tail)
+
+
+def test_large_radix_falls_back_when_arena_is_short():
+    """With no arena room for the bucket tables (8 B per pair) the direct
+    kernel runs; the result is the same."""
+    import torch
+    from paper_1505_01120_gb300 import scl
+    from paper_1505_01120_gb300.context import Context, current_stream
+    rng = np.random.default_rng(2200)
+    nk, n = 1 << 18, 1 << 21
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    vals = rng.random(n, dtype=np.float32)
+    # partition 16 MiB + tables 4 MiB fit; another 16 MiB for the buckets does not
+    with Context(24 << 20, device=0) as c:
+        st = current_stream(0)
+        p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+        (cnt, sums, s64, r), nl = _launches(
+            scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
+        assert nl == 2
+        assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+        scl.scl_free_partition(c.handle, p)
+    torch.cuda.synchronize()

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_1505_01120_gb300 import synth
 from gpu_common import check_f32_result, check_keyed
 
 pytestmark = pytest.mark.gpu
@@ -149,6 +150,23 @@ def test_keyed_ones_give_exact_counts_as_sums(env):
     p = scl.scl_load_partition_kv(c.handle, keys, np.ones(n, np.float32), stream=st)
     cnt, sums, s64, _ = scl.scl_keyed_reduce(c.handle, p, 4096, stream=st)
     assert np.all(cnt == 999) and np.all(sums == 999.0) and np.all(s64 == 999.0)
+
+
+@pytest.mark.parametrize("nk", [1, 32, 33, 4096])
+def test_keyed_zipf_keys(env, nk):
+    """Zipf(1.2) keys, id 0 the most frequent: the sums of ids below 32 go
+    through per-warp copies folded into the table.  Counts exact, sums within
+    the fp32 tolerance; one CTA and many pieces alike."""
+    c, scl, st, _ = env
+    rng = np.random.default_rng(111 + nk)
+    for n in (1000, 3_000_001):
+        keys = synth.zipf_keys_i32(n, rng, nk)
+        vals = rng.random(n, dtype=np.float32)
+        p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+        cnt, sums, s64, r = scl.scl_keyed_reduce(c.handle, p, nk, stream=st)
+        assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+        assert r.u64_sum == n and r.status == 0
+        scl.scl_free_partition(c.handle, p)
 
 
 def test_keyed_out_of_range_keys(env):
