@@ -296,9 +296,12 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
  * vocabulary, Sec. 3.2.3).  num_keys in [1, SCL_MAX_LARGE_KEYS].  Two paths:
  *   - bucket-partitioned, for partitions of 2^20 to 2^31 - 1 pairs whose key
  *     and value arrays are 16-byte aligned, over more than 4096 keys: the
- *     pairs are grouped by bucket (key / 4096) in a temporary copy, then
- *     every bucket is counted in a per-block shared-memory table.  Needs
- *     8 B per pair plus a few bytes per chunk and bucket from the arena;
+ *     pairs are grouped by bucket (4096 to 16384 consecutive ids) in a
+ *     temporary copy, then every bucket is counted in a per-block
+ *     shared-memory table; when ids below 1024 hold at least 1/8 of the
+ *     pairs (a vocabulary numbered by frequency) they are counted as the
+ *     pairs are read instead of being copied.  Needs 8 B per pair plus a
+ *     few bytes per chunk and bucket from the arena;
  *   - direct, otherwise or when the arena has no room for that copy: keys
  *     below 4096 (the frequent ids when words are numbered by frequency) go
  *     to a per-block shared-memory table, every other key straight to global

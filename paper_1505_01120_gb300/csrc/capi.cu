@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -481,22 +482,49 @@ static void* radix_tables(Ctx* c, Scratch& sc, size_t bytes, void** call_tmp) {
     return q;
 }
 
+// The scatter and the wider reduce tables need more than 48 KB of dynamic
+// shared memory: allow each variant its size once per device.
+static int prepare_radix() {
+    static std::mutex mu;
+    static std::vector<int> ready;
+    int dev = 0;
+    SCL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (std::find(ready.begin(), ready.end(), dev) != ready.end()) return SCL_OK;
+    for (uint32_t lt = kRadixMinLogT; lt <= kRadixMaxLogT; ++lt) {
+        for (int hot = 0; hot < 2; ++hot)
+            SCL_CUDA(cudaFuncSetAttribute(radix_scatter_fn(lt, hot != 0),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)radix_scatter_smem(kRadixMaxBuckets)));
+        SCL_CUDA(cudaFuncSetAttribute(radix_reduce_fn(lt),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)radix_reduce_smem(lt)));
+    }
+    ready.push_back(dev);
+    return SCL_OK;
+}
+
 // Histogram, scan, scatter and per-bucket reduce (radix.h).  *launched is
 // false, with nothing enqueued, when the arena has no room for the tables.
 static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, uint32_t* counts,
                         double* sums64, uint32_t* bad, cudaStream_t st, void** call_tmp,
                         bool* launched) {
     *launched = false;
-    const uint32_t nb = (nk + kMaxKeys - 1) / kMaxKeys;
-    const void* scatter = radix_scatter_fn(radix_staged(nb));
-    const size_t hist_smem = (size_t)nb * 4, scat_smem = radix_scatter_smem(nb);   // < 48 KB
+    SCL_TRY(prepare_radix());
+    // the bucket width depends only on num_keys; the chunking on the scatter's residency
+    const RadixGeometry g0 = radix_geometry(p.n, nk, 1);
+    const void* scatter = radix_scatter_fn(g0.log_t, false);
+    const void* scatter_hot = radix_scatter_fn(g0.log_t, true);
+    const void* reduce = radix_reduce_fn(g0.log_t);
+    const uint32_t rblock = radix_reduce_block(g0.log_t);
+    const size_t hist_smem = radix_hist_smem(g0.nb), scat_smem = radix_scatter_smem(g0.nb);
+    const size_t red_smem = radix_reduce_smem(g0.log_t);
     int occ_h = 0, occ_s = 0, occ_r = 0;
     SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, radix_hist_fn(), kRadixBlock,
                                                            hist_smem));
     SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, scatter, kRadixBlock,
                                                            scat_smem));
-    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, radix_reduce_fn(), kRadixBlock,
-                                                           0));
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, reduce, rblock, red_smem));
     const uint32_t slots_h = (uint32_t)c->sms * std::max(occ_h, 1);
     const uint32_t slots_s = (uint32_t)c->sms * std::max(occ_s, 1);
     const uint32_t slots_r = (uint32_t)c->sms * std::max(occ_r, 1);
@@ -513,10 +541,14 @@ static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, ui
     r.nb = g.nb;
     r.chunk = g.chunk;
     r.nchunks = g.nchunks;
+    r.log_t = g.log_t;
+    r.fixed = radix_bucket_cost(g.log_t);
     r.bk = reinterpret_cast<uint32_t*>(t + l.bk);
     r.hist = reinterpret_cast<uint32_t*>(t + l.hist);
     r.tot = reinterpret_cast<uint32_t*>(t + l.tot);
     r.bstart = reinterpret_cast<uint32_t*>(t + l.bstart);
+    r.bcost = reinterpret_cast<uint32_t*>(t + l.bcost);
+    r.mode = reinterpret_cast<uint32_t*>(t + l.mode);
     r.counts = counts;
     r.sums64 = sums64;
     r.ticket = sc.hdr + H_RADIX_TICKET;   // reset to zero by the scan's last CTA
@@ -525,12 +557,16 @@ static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, ui
     SCL_CUDA(cudaLaunchKernel(radix_hist_fn(), dim3(std::min(g.nchunks, slots_h)),
                               dim3(kRadixBlock), params, hist_smem, st));
     const uint32_t rows = kRadixScanBlock / 32;   // one warp per bucket row
-    SCL_CUDA(cudaLaunchKernel(radix_scan_fn(), dim3((g.nb + rows - 1) / rows),
+    SCL_CUDA(cudaLaunchKernel(radix_scan_fn(), dim3((g.nb + 1 + rows - 1) / rows),
                               dim3(kRadixScanBlock), params, 0, st));
+    // the scan chose one form (hot ids bypassing the partition or not); the
+    // other returns at once
     SCL_CUDA(cudaLaunchKernel(scatter, dim3(std::min(g.nchunks, slots_s)), dim3(kRadixBlock),
                               params, scat_smem, st));
-    SCL_CUDA(cudaLaunchKernel(radix_reduce_fn(), dim3(slots_r), dim3(kRadixBlock), params, 0, st));
-    count_launches(4);
+    SCL_CUDA(cudaLaunchKernel(scatter_hot, dim3(std::min(g.nchunks, slots_s)), dim3(kRadixBlock),
+                              params, scat_smem, st));
+    SCL_CUDA(cudaLaunchKernel(reduce, dim3(slots_r), dim3(rblock), params, red_smem, st));
+    count_launches(5);
     *launched = true;
     return SCL_OK;
 }

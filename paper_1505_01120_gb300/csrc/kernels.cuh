@@ -291,6 +291,22 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
 
 // ------------------------------------------------------------ keyed piece
 
+// Adds the head copies of ids [0, nhead) into the table's fp32 sums and
+// clears them.  Warp w owns copies w * kKeyedHeadClasses onwards; lane l sums
+// its warp's copies of id l and adds them with one atomic, so the warps fold
+// in parallel.  Call between barriers.
+__device__ __forceinline__ void fold_head_copies(float* heads, float* sum, uint32_t nhead) {
+    const uint32_t lane = threadIdx.x & 31;
+    float* own = heads + (threadIdx.x >> 5) * kKeyedHeadClasses * kKeyedHeadStride;
+    float t = 0.f;
+#pragma unroll
+    for (uint32_t r = 0; r < kKeyedHeadClasses; ++r) {
+        t += own[r * kKeyedHeadStride + lane];
+        own[r * kKeyedHeadStride + lane] = 0.f;
+    }
+    if (t != 0.f && lane < nhead) atomicAdd(&sum[lane], t);
+}
+
 // Counts go straight to the table (integer adds to one address do not
 // serialise); fp32 sums of ids below kKeyedHead go to this thread's head copy
 // (`head`), the rest to the table.  Hashed ids spread the frequent keys, so
@@ -315,7 +331,6 @@ template <int BLOCK, int IPT, bool HASHED>
 __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, uint64_t e,
                                                 uint32_t* tab) {
     constexpr uint32_t CH = BLOCK * IPT * 4;
-    constexpr uint32_t NCOPY = BLOCK / 32 * kKeyedHeadClasses;
     static_assert(kKeyedHeadWords(BLOCK) * 4 + kKeyedTableWords * 4 <= kKeyedSmemBytes, "smem");
     uint32_t* cnt = tab;
     float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
@@ -365,11 +380,7 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
     }
     const int any_bad = __syncthreads_or((int)bad);
     if (!HASHED) {
-        for (uint32_t k = threadIdx.x; k < min(nk, kKeyedHead); k += BLOCK) {
-            float h = 0.f;
-            for (uint32_t r = 0; r < NCOPY; ++r) h += heads[r * kKeyedHeadStride + k];
-            sum[k] += h;
-        }
+        fold_head_copies(heads, sum, min(nk, kKeyedHead));
         __syncthreads();
     }
     return any_bad;
@@ -744,7 +755,6 @@ __device__ __forceinline__ void large_add(uint32_t k, uint32_t vbits, const Larg
 // its non-zero entries to global memory.
 template <bool ALIGNED>
 __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ LargeKeyedArgs a) {
-    constexpr uint32_t NCOPY = 256 / 32 * kKeyedHeadClasses;
     __shared__ uint32_t hc[kMaxKeys];
     __shared__ float hs[kMaxKeys];
     __shared__ float heads[kKeyedHeadWords(256)];
@@ -785,14 +795,13 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
             large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, hc, hs,
                       head, bad);
         __syncthreads();
+        fold_head_copies(heads, hs, min(hot, kKeyedHead));
+        __syncthreads();
         for (uint32_t k = threadIdx.x; k < hot; k += blockDim.x) {
             const uint32_t c = hc[k];
             if (c) {
-                float t = hs[k];
-                if (k < kKeyedHead)
-                    for (uint32_t r = 0; r < NCOPY; ++r) t += heads[r * kKeyedHeadStride + k];
                 atomicAdd(&a.counts[k], c);
-                atomicAdd(&a.sums64[k], (double)t);
+                atomicAdd(&a.sums64[k], (double)hs[k]);
             }
         }
         __syncthreads();   // the table is zeroed again by the next piece

@@ -8,8 +8,9 @@
 //   * the range allocator against a reference bitmap under random use;
 //   * the bucket-partitioned large-key reduce: its geometry and table layout,
 //     and, replaying the four passes' offset arithmetic on random keys, that
-//     every kept pair is written once inside its bucket and read once by
-//     the reduce's CTA shares, with no index outside the tables.
+//     every partitioned pair is written once inside its bucket and read once
+//     by the reduce's cost shares (hot ids counted apart), with no index
+//     outside the tables and no share far above its cost.
 // Prints "ok" and exits 0, or names the first failed check and exits 1.
 #include <stdio.h>
 #include <stdlib.h>
@@ -182,8 +183,18 @@ static void check_radix() {
         CHECK(g.chunk % kRadixChunkAlign == 0 && g.chunk >= kRadixChunkAlign, "chunk %u", g.chunk);
         CHECK((uint64_t)g.nchunks * g.chunk >= n && (uint64_t)(g.nchunks - 1) * g.chunk < n,
               "chunks do not cover n %llu", (unsigned long long)n);
-        CHECK(g.nb >= 2 && (uint64_t)g.nb * kMaxKeys >= nk && (uint64_t)(g.nb - 1) * kMaxKeys < nk,
-              "buckets %u for %u keys", g.nb, nk);
+        CHECK(g.log_t >= kRadixMinLogT && g.log_t <= kRadixMaxLogT, "log_t %u", g.log_t);
+        CHECK(g.nb >= 2 && g.nb <= kRadixMaxBuckets && ((uint64_t)g.nb << g.log_t) >= nk &&
+                  ((uint64_t)(g.nb - 1) << g.log_t) < nk,
+              "buckets %u of 2^%u for %u keys", g.nb, g.log_t, nk);
+        CHECK(g.log_t == kRadixMinLogT ||
+                  (((uint64_t)nk + (1u << (g.log_t - 1)) - 1) >> (g.log_t - 1)) >
+                      kRadixPreferredBuckets,
+              "buckets wider than needed: 2^%u for %u keys", g.log_t, nk);
+        CHECK(g.nb <= kRadixPreferredBuckets || g.log_t == kRadixMaxLogT,
+              "%u buckets of 2^%u", g.nb, g.log_t);
+        CHECK(radix_reduce_smem(g.log_t) <= 227 * 1024, "reduce shared memory %u",
+              radix_reduce_smem(g.log_t));
         CHECK(g.nchunks <= 2ull * slots + 1 || g.chunk == kRadixChunkAlign, "too many chunks");
         const RadixLayout l = radix_layout(n, g);
         CHECK(l.hist >= n * 8 + 8 || (n % 2 == 0 && l.hist >= n * 8),
@@ -196,11 +207,14 @@ static void check_radix() {
               radix_scatter_smem(g.nb));
     }
     // replay of the passes' offsets (scaled-down sizes, same formulas)
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < 48; ++it) {
         const uint64_t n = kRadixMinPairs + rng() % (3 * kRadixMinPairs);
         const uint32_t shape = it % 4;
-        const uint32_t nk = shape == 0 ? kMaxKeys + 1 + (uint32_t)(rng() % 10)
-                                       : kMaxKeys * (2 + (uint32_t)(rng() % 300)) - (uint32_t)(rng() % 7);
+        const uint32_t space = (it / 4) % 4;
+        const uint32_t nk = space == 0 ? kMaxKeys + 1 + (uint32_t)(rng() % 10)
+                            : space == 1 ? kMaxLargeKeys - (uint32_t)(rng() % 5000)   // 2^14 ids
+                            : space == 2 ? (1u << 22) + 1 + (uint32_t)(rng() % 1000)  // 2^13 ids
+                                         : kMaxKeys * (2 + (uint32_t)(rng() % 300)) - (uint32_t)(rng() % 7);
         const uint32_t slots = 64 + (uint32_t)(rng() % 800), grid4 = 64 + (uint32_t)(rng() % 800);
         const RadixGeometry g = radix_geometry(n, nk, slots);
         std::vector<uint32_t> keys(n);
@@ -210,33 +224,43 @@ static void check_radix() {
                              : (uint32_t)(rng() % (nk + nk / 50)); // some out of range
         }
         if (shape == 3) std::sort(keys.begin(), keys.end());
-        // pass 1 + scan
-        std::vector<uint32_t> hist((size_t)g.nb * g.nchunks, 0), bstart(g.nb + 1, 0);
+        // pass 1 (row nb: hot ids) + scan, and the scan's choice of form
+        std::vector<uint32_t> hist((size_t)(g.nb + 1) * g.nchunks, 0), tot(g.nb + 1, 0),
+            bstart(g.nb + 1, 0);
         for (uint32_t c = 0; c < g.nchunks; ++c)
             for (uint64_t i = (uint64_t)c * g.chunk; i < std::min<uint64_t>(n, (uint64_t)(c + 1) * g.chunk); ++i)
-                if (keys[i] < nk) ++hist[(size_t)(keys[i] / kMaxKeys) * g.nchunks + c];
-        for (uint32_t b = 0; b < g.nb; ++b) {
+                if (keys[i] < nk)
+                    ++hist[(size_t)(keys[i] < kRadixHotIds ? g.nb : keys[i] >> g.log_t) * g.nchunks + c];
+        for (uint32_t b = 0; b <= g.nb; ++b) {
             uint32_t run = 0;
             for (uint32_t c = 0; c < g.nchunks; ++c) {
                 const uint32_t v = hist[(size_t)b * g.nchunks + c];
                 hist[(size_t)b * g.nchunks + c] = run;
                 run += v;
             }
-            bstart[b + 1] = bstart[b] + run;
+            tot[b] = run;
         }
+        uint64_t kept = 0;
+        for (uint32_t b = 0; b < g.nb; ++b) kept += tot[b];
+        const bool hot_on = tot[g.nb] != 0 && (uint64_t)tot[g.nb] * 8 >= kept + tot[g.nb];
+        if (it == 5) CHECK(hot_on, "one-bucket keys 0..2 should bypass the partition");
+        for (uint32_t b = 0; b < g.nb; ++b)
+            bstart[b + 1] = bstart[b] + tot[b] + (b == 0 && !hot_on ? tot[g.nb] : 0u);
         const uint64_t nv = bstart[g.nb];
         // pass 3: each chunk's tiles advance per-bucket cursors
         std::vector<uint32_t> owner(nv, UINT32_MAX);
         for (uint32_t c = 0; c < g.nchunks; ++c) {
             std::vector<uint32_t> cur(g.nb);
-            for (uint32_t b = 0; b < g.nb; ++b) cur[b] = bstart[b] + hist[(size_t)b * g.nchunks + c];
+            for (uint32_t b = 0; b < g.nb; ++b)
+                cur[b] = bstart[b] + hist[(size_t)b * g.nchunks + c] +
+                         (b == 0 && !hot_on ? hist[(size_t)g.nb * g.nchunks + c] : 0u);
             const uint64_t e0 = std::min<uint64_t>(n, (uint64_t)(c + 1) * g.chunk);
             for (uint64_t t0 = (uint64_t)c * g.chunk; t0 < e0; t0 += kRadixTile) {
                 uint32_t tn = 0;
                 for (uint64_t i = t0; i < std::min<uint64_t>(e0, t0 + kRadixTile); ++i) {
-                    if (keys[i] >= nk) continue;
+                    if (keys[i] >= nk || (hot_on && keys[i] < kRadixHotIds)) continue;   // hot table
                     ++tn;
-                    const uint32_t b = keys[i] / kMaxKeys;
+                    const uint32_t b = keys[i] >> g.log_t;
                     const uint64_t pos = cur[b]++;
                     CHECK(pos >= bstart[b] && pos < bstart[b + 1], "pair %llu outside its bucket",
                           (unsigned long long)i);
@@ -249,25 +273,43 @@ static void check_radix() {
         }
         for (uint64_t q = 0; q < nv; ++q) CHECK(owner[q] != UINT32_MAX, "position %llu unwritten",
                                                 (unsigned long long)q);
-        // pass 4: even CTA shares, bucket search, pieces of at most kLargePiece
+        // cost starts as the scan's last CTA forms them
+        const uint32_t fixed = radix_bucket_cost(g.log_t);
+        std::vector<uint64_t> bcost(g.nb + 1, 0);
+        for (uint32_t b = 0, ne = 0; b <= g.nb; ++b) {
+            bcost[b] = bstart[b] + (uint64_t)ne * fixed;
+            if (b < g.nb && bstart[b + 1] > bstart[b]) ++ne;
+        }
+        CHECK(bcost[g.nb] < (1ull << 32), "cost overflows 32 bits");
+        // pass 4: even shares of cost, bucket search, pieces of at most kLargePiece
         std::vector<uint32_t> cnt(nk, 0), seen(nv, 0);
+        if (hot_on)
+            for (uint32_t k : keys)   // the scatter's hot table
+                if (k < kRadixHotIds) ++cnt[k];
+        const uint64_t ctot = bcost[g.nb];
+        uint64_t most = 0;
         for (uint32_t blk = 0; blk < grid4; ++blk) {
-            const uint64_t lo = nv * blk / grid4, hi = nv * (blk + 1) / grid4;
-            if (lo >= hi) continue;
+            const uint64_t clo = ctot * blk / grid4, chi = ctot * (blk + 1) / grid4;
+            if (clo >= chi) continue;
             uint32_t bl = 0, bh = g.nb - 1;
             while (bl < bh) {
                 const uint32_t mid = (bl + bh + 1) / 2;
-                if (bstart[mid] <= lo) bl = mid;
+                if (bcost[mid] <= clo) bl = mid;
                 else bh = mid - 1;
             }
-            CHECK(bstart[bl] <= lo && lo < bstart[bl + 1], "search missed pair %llu",
-                  (unsigned long long)lo);
-            uint64_t s = lo;
-            for (uint32_t b = bl; s < hi && b < g.nb; ++b) {
-                const uint64_t bend = std::min<uint64_t>(bstart[b + 1], nv);
-                if (bend <= s) continue;
-                const uint64_t se = std::min(hi, bend);
-                const uint32_t hot = std::min(kMaxKeys, nk - b * kMaxKeys);
+            CHECK(bcost[bl] <= clo, "search overshot cost %llu", (unsigned long long)clo);
+            uint64_t work = 0;
+            for (uint32_t b = bl; b < g.nb && bcost[b] < chi; ++b) {
+                const uint64_t nbk = bstart[b + 1] - bstart[b];
+                if (!nbk) continue;
+                const uint64_t first = bcost[b] + fixed;
+                const uint64_t j0 = clo > first ? std::min(clo - first, nbk) : 0;
+                const uint64_t j1 = chi > first ? std::min(chi - first, nbk) : 0;
+                if (j0 >= j1) continue;
+                work += j1 - j0 + fixed;
+                const uint64_t s = bstart[b] + j0, se = bstart[b] + j1;
+                const uint32_t T = 1u << g.log_t;
+                const uint32_t hot = std::min(T, nk - b * T);
                 for (uint64_t p0 = s; p0 < se; p0 += kLargePiece) {
                     const uint64_t p1 = std::min(p0 + kLargePiece, se);
                     // 16-byte loads of two pairs: words [4 q, 4 q + 4)
@@ -275,16 +317,19 @@ static void check_radix() {
                     CHECK((q1 - 1) * 16 + 16 <= radix_layout(n, g).hist, "load past bk");
                     for (uint64_t i = p0; i < p1; ++i) {
                         const uint32_t k = owner[i];
-                        CHECK(k / kMaxKeys == b && k % kMaxKeys < hot, "pair %llu in bucket %u",
+                        CHECK((k >> g.log_t) == b && (k & (T - 1)) < hot, "pair %llu in bucket %u",
                               (unsigned long long)i, b);
                         ++seen[i];
                         ++cnt[k];
                     }
                     (void)q0;
                 }
-                s = se;
             }
+            most = std::max(most, work);
         }
+        // no CTA gets much more than its share of the cost (one bucket's table at most)
+        CHECK(most <= ctot / grid4 + 2ull * fixed + 2, "CTA work %llu, share %llu",
+              (unsigned long long)most, (unsigned long long)(ctot / grid4));
         for (uint64_t q = 0; q < nv; ++q) CHECK(seen[q] == 1, "pair %llu reduced %u times",
                                                 (unsigned long long)q, seen[q]);
         std::vector<uint32_t> ref(nk, 0);

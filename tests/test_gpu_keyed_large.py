@@ -136,9 +136,20 @@ def _launches(scl, fn):
 
 
 # Bucket-partitioned path (partitions of at least 2^20 aligned pairs over more
-# than 4096 keys): histogram, scan, scatter and per-bucket reduce kernels,
-# then the finishing pass -- 5 launches; the direct path makes 2.
+# than 4096 keys): histogram, scan, the two scatter forms (one of them returns
+# at once), the per-bucket reduce, then the finishing pass -- 6 launches; the
+# direct path makes 2.
 RADIX_CASES = {
+    # every pair on an id below 1024: counted in the scatter's hot tables, the
+    # partition stays empty
+    "all_hot": lambda rng: (1 << 20, rng.integers(0, 1024, (1 << 20) + 9, dtype=np.int32)),
+    # ids on both sides of the hot limit (1022 .. 1026): hot ids bypass
+    "hot_edge": lambda rng: (5000, rng.integers(1022, 1027, (1 << 20) + 2, dtype=np.int32)),
+    # hot ids just under 1/8 of the pairs: no bypass, they go through bucket 0
+    "few_hot": lambda rng: (1 << 20, np.where(rng.random((1 << 20) + 3) < 0.12,
+                                              rng.integers(0, 1024, (1 << 20) + 3),
+                                              rng.integers(1024, 1 << 20, (1 << 20) + 3)
+                                              ).astype(np.int32)),
     # one key for every pair: a single bucket split over the whole grid
     "one_key": lambda rng: (1 << 20, np.full((1 << 20) + 3, 777_777, np.int32)),
     # only the last, partial bucket (3 keys) is used
@@ -148,8 +159,19 @@ RADIX_CASES = {
     # odd length: ragged tails in every pass
     "odd_length": lambda rng: (1 << 20, rng.integers(0, 1 << 20, (1 << 20) + 12_345,
                                                     dtype=np.int32)),
-    # 4096 buckets, most of them holding a few hundred pairs
-    "max_buckets": lambda rng: (1 << 24, rng.integers(0, 1 << 24, 1 << 21, dtype=np.int32)),
+    # 2^24 keys: 1024 buckets of 16384 ids, a few pairs per id
+    "max_keys": lambda rng: (1 << 24, rng.integers(0, 1 << 24, 1 << 21, dtype=np.int32)),
+    # 2^24 keys, Zipf: the hot ids in bucket 0 of the widest table
+    "max_keys_zipf": lambda rng: (1 << 24, synth.zipf_keys_i32(1 << 21, rng, 1 << 24)),
+    # 2^23 + 1 keys: 513 buckets of 16384 ids, the last holding one id (two
+    # buckets per thread in the tile scan)
+    "wide_buckets": lambda rng: ((1 << 23) + 1,
+                                 rng.integers(0, (1 << 23) + 1, (1 << 20) + 5, dtype=np.int32)),
+    # 2^22 keys: 256 buckets of 16384 ids
+    "mid_buckets": lambda rng: (1 << 22, rng.integers(0, 1 << 22, 3 << 20, dtype=np.int32)),
+    # 2^21 + 7 keys: 257 buckets of 8192 ids, the last holding 7
+    "buckets_8192": lambda rng: ((1 << 21) + 7,
+                                 rng.integers(0, (1 << 21) + 7, (1 << 21) + 3, dtype=np.int32)),
     # sorted keys: CTAs that hold whole buckets store them without atomics
     "sorted": lambda rng: (1 << 22, np.sort(rng.integers(0, 1 << 22, 1 << 21,
                                                          dtype=np.int32))),
@@ -170,7 +192,7 @@ def test_large_radix_cases(env, case):
     p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
     (cnt, sums, s64, r), nl = _launches(
         scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
-    assert nl == 5
+    assert nl == 6
     assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
     assert r.status == 0 and r.u64_sum == keys.size and r.n == keys.size
     scl.scl_free_partition(c.handle, p)
@@ -214,7 +236,7 @@ def test_large_radix_and_direct_agree(env):
                                                                         stream=st))
     (b, bs, b64, _), nb_ = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, tail, nk,
                                                                             stream=st))
-    assert (na, nb_) == (5, 2)
+    assert (na, nb_) == (6, 2)
     ref = np.bincount(keys, minlength=nk).astype(np.uint32)
     assert np.array_equal(a, ref)
     ref[keys[0]] -= 1
