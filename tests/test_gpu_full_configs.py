@@ -5,6 +5,11 @@
   partition against the oracle, on the first and on a later replay.
 * 16 x 16,777,216 (key, value) pairs, keyed count+sum in one batch launch:
   every partition's table against the oracle.
+* 16 x 4,194,304 pairs with Zipf(1.2) keys over 4096 ids, one batch launch:
+  every partition's table against the oracle.
+* 67,108,864 pairs over 2^20 keys (uniform and Zipf), the bucket-partitioned
+  large-key reduce on device tables as the benchmark calls it: the whole table
+  against the oracle.
 * The 10,000-task uneven batch (log-normal sizes, kernel uniform over three),
   graph replay: every task against the oracle.
 * The serving pool (240 partitions, log-normal sizes up to 2^26 elements)
@@ -91,6 +96,58 @@ def test_keyed_16x16777216_one_launch(env):
         assert int(res[i]["status"]) == 0 and int(res[i]["u64_sum"]) == m
         assert check_keyed(h[i, :4096].view(np.uint32), h[i, 4096:8192].view(np.float32),
                            h[i, 8192:].view(np.float64), keys[i], vals[i], 4096) == 0
+
+
+def test_keyed_zipf_16x4194304_one_launch(env):
+    c, scl, st, torch = env
+    parts_n, m, nk = 16, 1 << 22, 4096
+    rng = np.random.default_rng(12)
+    keys = synth.zipf_keys_i32(parts_n * m, rng, nk).reshape(parts_n, m)
+    vals = synth.unit_f32(parts_n * m, rng).reshape(parts_n, m)
+    outs = torch.zeros((parts_n, nk * 4), dtype=torch.int32, device="cuda")
+    parts, tasks = [], []
+    for i in range(parts_n):
+        p = scl.scl_load_partition_kv(c.handle, keys[i], vals[i], stream=st)
+        base = outs[i].data_ptr()
+        parts.append(p)
+        tasks.append(dict(part=p, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM,
+                          num_keys=nk, counts_out=base, sums_out=base + nk * 4,
+                          sums64_out=base + nk * 8))
+    b = scl.scl_batch_create(c.handle, scl.make_tasks(tasks), parts_n)
+    scl.scl_batch_launch(b, st)
+    res = scl.scl_batch_results(b, parts_n, stream=st)
+    scl.scl_batch_destroy(b)
+    h = outs.cpu().numpy()
+    for p in parts:
+        scl.scl_free_partition(c.handle, p)
+    for i in range(parts_n):
+        assert int(res[i]["status"]) == 0 and int(res[i]["u64_sum"]) == m
+        assert check_keyed(h[i, :nk].view(np.uint32), h[i, nk:2 * nk].view(np.float32),
+                           h[i, 2 * nk:].view(np.float64), keys[i], vals[i], nk) == 0
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_keyed_large_1048576_keys_67108864(env, dist):
+    c, scl, st, torch = env
+    nk, n = 1 << 20, 1 << 26
+    rng = np.random.default_rng(10)
+    keys = synth.keys_i32(n, rng, nk) if dist == "uniform" else synth.zipf_keys_i32(n, rng, nk)
+    vals = synth.unit_f32(n, rng)
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    dc = torch.empty(nk, dtype=torch.int32, device="cuda")
+    ds = torch.empty(nk, dtype=torch.float32, device="cuda")
+    d64 = torch.empty(nk, dtype=torch.float64, device="cuda")
+    dr = torch.empty(48, dtype=torch.uint8, device="cuda")
+    for _ in range(2):   # the second call reuses the stream's bucket copy
+        before = scl.scl_kernel_launches_total()
+        scl.scl_keyed_reduce_large_async(c.handle, p, nk, dc, ds, d64, dr, stream=st)
+        assert scl.scl_kernel_launches_total() - before == 6   # the partitioned path
+        torch.cuda.synchronize()
+        assert check_keyed(dc.cpu().numpy().view(np.uint32), ds.cpu().numpy(),
+                           d64.cpu().numpy(), keys, vals, nk) == 0
+        r = dr.cpu().numpy().view(scl.RESULT_DTYPE)[0]
+        assert int(r["status"]) == 0 and int(r["u64_sum"]) == n
+    scl.scl_free_partition(c.handle, p)
 
 
 def test_batch_10000_graph_replay(env):

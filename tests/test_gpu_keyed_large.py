@@ -266,3 +266,30 @@ def test_large_radix_falls_back_when_arena_is_short():
         assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
         scl.scl_free_partition(c.handle, p)
     torch.cuda.synchronize()
+
+
+def test_large_async_buffer_grows_and_is_reused(env):
+    """The async form keeps its bucket copy per stream: a larger partition
+    grows it (after the device drains), a smaller one reuses it; every table
+    exact in counts."""
+    c, scl, st, torch = env
+    rng = np.random.default_rng(2300)
+    nk = 1 << 18
+    s2 = torch.cuda.Stream()
+    dc = torch.empty(nk, dtype=torch.int32, device="cuda")
+    ds = torch.empty(nk, dtype=torch.float32, device="cuda")
+    d64 = torch.empty(nk, dtype=torch.float64, device="cuda")
+    dr = torch.empty(48, dtype=torch.uint8, device="cuda")
+    for n in ((1 << 20) + 5, 3 << 20, (1 << 20) + 77):
+        keys = rng.integers(0, nk, size=n, dtype=np.int32)
+        vals = rng.random(n, dtype=np.float32)
+        p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+        torch.cuda.synchronize()
+        before = scl.scl_kernel_launches_total()
+        scl.scl_keyed_reduce_large_async(c.handle, p, nk, dc, ds, d64, dr, stream=s2.cuda_stream)
+        nl = scl.scl_kernel_launches_total() - before
+        torch.cuda.synchronize()
+        assert nl == 6
+        assert check_keyed(dc.cpu().numpy().view(np.uint32), ds.cpu().numpy(),
+                           d64.cpu().numpy(), keys, vals, nk) == 0
+        scl.scl_free_partition(c.handle, p)
