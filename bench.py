@@ -17,7 +17,8 @@ Also reported on the same line:
                 record), plus the same call on a thread per core
                 (``all_cores``) and the host's core count and CPU model
   configs       the other workloads: the autotuner; mix32 on 1,048,576 uint32
-                (latency) and on 256 x 1,048,576 (GB/s); keyed count+sum on
+                (latency: the synchronous call, and the kernel alone from a
+                CUDA graph replay) and on 256 x 1,048,576 (GB/s); keyed count+sum on
                 16 x 16,777,216 pairs, on Zipf(1.2) keys, with hashed keys,
                 and over 2^20 keys (bucket-partitioned);
                 the materialised map; the vector-add ReduceCL; 10,000 uneven
@@ -305,11 +306,22 @@ def extra_configs(torch, scl, ctx, stream, pk, full: bool) -> dict:
         scl.scl_map_reduce(ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, stream=st)
         lat.append((time.perf_counter() - t0) * 1e6)
     dres = torch.zeros(48, dtype=torch.uint8, device="cuda")
-    kus = time_device(torch, stream, lambda: scl.scl_map_reduce_async(
-        ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, dres.data_ptr(), stream=st), 50) * 1e3
+    call = lambda: scl.scl_map_reduce_async(  # noqa: E731
+        ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, dres.data_ptr(), stream=st)
+    # events around one host call: the device idles while the host enqueues
+    enq_us = time_device(torch, stream, call, 50) * 1e3
+    # device time per call: 20 calls captured back to back in a CUDA graph
+    call()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for _ in range(20):
+            call()
+    kus = time_device(torch, stream, g.replay, 20) / 20 * 1e3
     out["mix32_u64_sum_1x1048576"] = {
         "bit_exact_vs_oracle": bool(exact), "sync_call_p50_us": float(np.percentile(lat, 50)),
-        "sync_call_p99_us": float(np.percentile(lat, 99)), "kernel_us": kus}
+        "sync_call_p99_us": float(np.percentile(lat, 99)), "kernel_us": kus,
+        "enqueue_and_kernel_us": enq_us}
     scl.scl_free_partition(ctx.handle, p)
 
     # mix32 scaled: 256 x 1,048,576 in one launch (batch of 256)

@@ -593,14 +593,16 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
     a.result = res;
     a.ticket = sc.hdr + H_LARGE_TICKET;   // reset to zero by the finishing pass
     a.bad = sc.hdr + H_LARGE_BAD;
-    SCL_CUDA(cudaMemsetAsync(counts, 0, (size_t)nk * 4, st));
-    SCL_CUDA(cudaMemsetAsync(sums64, 0, (size_t)nk * 8, st));
     SCL_CUDA(cudaMemsetAsync(res, 0, sizeof(scl_result), st));
     SCL_CUDA(cudaMemsetAsync(a.bad, 0, 4, st));
     void* params[] = {&a};
-    bool done = false;
+    bool done = false;   // the partitioned path zeroes the output tables in its first kernel
     if (a.aligned && nk > kMaxKeys && p.n >= kRadixMinPairs && p.n <= kRadixMaxPairs)
         SCL_TRY(launch_radix(ctx, sc, p, nk, counts, sums64, a.bad, st, call_tmp, &done));
+    if (!done) {
+        SCL_CUDA(cudaMemsetAsync(counts, 0, (size_t)nk * 4, st));
+        SCL_CUDA(cudaMemsetAsync(sums64, 0, (size_t)nk * 8, st));
+    }
     if (p.n && !done) {
         const void* fn = large_keyed_kernel_fn(a.aligned);
         int nb = 0;
@@ -611,8 +613,10 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
         SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(256), params, 0, st));
         count_launches(1);
     }
+    // two CTAs per SM: each CTA adds its totals with three atomics on the same
+    // three words, so fewer CTAs wait less on them
     const uint32_t fgrid = (uint32_t)std::max<uint64_t>(
-        1, std::min<uint64_t>(((uint64_t)nk + 255) / 256, (uint64_t)ctx->sms * 8));
+        1, std::min<uint64_t>(((uint64_t)nk + 255) / 256, (uint64_t)ctx->sms * 2));
     SCL_CUDA(cudaLaunchKernel(large_keyed_finish_fn(), dim3(fgrid), dim3(256), params, 0, st));
     count_launches(1);
     return SCL_OK;

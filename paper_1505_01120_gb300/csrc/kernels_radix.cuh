@@ -57,12 +57,17 @@ __device__ __forceinline__ uint4 radix_load4(const char* base, I i, I e, uint32_
 }
 
 // Pass 1: per chunk, pairs per bucket, pairs of hot ids (below kRadixHotIds)
-// counted apart in row nb (bucket-major rows of hist).
+// counted apart in row nb (bucket-major rows of hist); zeroes the outputs.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_radix_hist(const __grid_constant__ RadixArgs a) {
     extern __shared__ uint32_t hist[];   // [nb + 1]
     const uint32_t rows = a.nb + 1;
     uint32_t bad = 0;
+    // the output tables start at zero (read first by pass 3's hot flushes)
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.num_keys; i += gridDim.x * BLOCK) {
+        a.counts[i] = 0u;
+        a.sums64[i] = 0.0;
+    }
     for (uint32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
         for (uint32_t i = threadIdx.x; i < rows; i += BLOCK) hist[i] = 0u;
         __syncthreads();

@@ -150,8 +150,8 @@ struct RadixArgs {
     uint32_t* bcost;          // [nb + 1] bucket starts in cost (< 2^32: n + nb * fixed)
     uint32_t* mode;           // 1: hot ids bypass the partition (set by the scan)
     uint32_t* bk;             // [2n] pairs {key % 2^log_t, value bits}, grouped by bucket
-    uint32_t* counts;         // [num_keys], zeroed before pass 4
-    double* sums64;           // [num_keys], zeroed before pass 4
+    uint32_t* counts;         // [num_keys], zeroed by pass 1
+    double* sums64;           // [num_keys], zeroed by pass 1
     uint32_t* ticket;         // zero between launches (scan's last CTA)
     uint32_t* bad;            // kRadixBadKey | kRadixBadPlace, zeroed before pass 1
 };
