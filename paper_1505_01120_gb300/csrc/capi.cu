@@ -495,7 +495,7 @@ static int prepare_radix() {
         for (int hot = 0; hot < 2; ++hot)
             SCL_CUDA(cudaFuncSetAttribute(radix_scatter_fn(lt, hot != 0),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)radix_scatter_smem(kRadixMaxBuckets)));
+                                          (int)radix_scatter_smem(kRadixMaxBuckets, hot != 0)));
         SCL_CUDA(cudaFuncSetAttribute(radix_reduce_fn(lt),
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)radix_reduce_smem(lt)));
@@ -517,16 +517,21 @@ static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, ui
     const void* scatter_hot = radix_scatter_fn(g0.log_t, true);
     const void* reduce = radix_reduce_fn(g0.log_t);
     const uint32_t rblock = radix_reduce_block(g0.log_t);
-    const size_t hist_smem = radix_hist_smem(g0.nb), scat_smem = radix_scatter_smem(g0.nb);
+    const size_t hist_smem = radix_hist_smem(g0.nb);
+    const size_t scat_smem = radix_scatter_smem(g0.nb, false);
+    const size_t scat_hot_smem = radix_scatter_smem(g0.nb, true);
     const size_t red_smem = radix_reduce_smem(g0.log_t);
-    int occ_h = 0, occ_s = 0, occ_r = 0;
+    int occ_h = 0, occ_s = 0, occ_sh = 0, occ_r = 0;
     SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, radix_hist_fn(), kRadixBlock,
                                                            hist_smem));
     SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, scatter, kRadixBlock,
                                                            scat_smem));
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sh, scatter_hot, kRadixBlock,
+                                                           scat_hot_smem));
     SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, reduce, rblock, red_smem));
     const uint32_t slots_h = (uint32_t)c->sms * std::max(occ_h, 1);
     const uint32_t slots_s = (uint32_t)c->sms * std::max(occ_s, 1);
+    const uint32_t slots_sh = (uint32_t)c->sms * std::max(occ_sh, 1);
     const uint32_t slots_r = (uint32_t)c->sms * std::max(occ_r, 1);
     const RadixGeometry g = radix_geometry(p.n, nk, slots_s);
     const RadixLayout l = radix_layout(p.n, g);
@@ -563,8 +568,8 @@ static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, ui
     // other returns at once
     SCL_CUDA(cudaLaunchKernel(scatter, dim3(std::min(g.nchunks, slots_s)), dim3(kRadixBlock),
                               params, scat_smem, st));
-    SCL_CUDA(cudaLaunchKernel(scatter_hot, dim3(std::min(g.nchunks, slots_s)), dim3(kRadixBlock),
-                              params, scat_smem, st));
+    SCL_CUDA(cudaLaunchKernel(scatter_hot, dim3(std::min(g.nchunks, slots_sh)), dim3(kRadixBlock),
+                              params, scat_hot_smem, st));
     SCL_CUDA(cudaLaunchKernel(reduce, dim3(slots_r), dim3(rblock), params, red_smem, st));
     count_launches(5);
     *launched = true;
@@ -676,6 +681,8 @@ int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void*
     if (tmp) ctx->arena.release(tmp);
     if (st != SCL_OK) return st;
     if (result) *result = *ctx->h_result;
+    if (ctx->h_result->status == SCL_E_TIMEOUT)
+        return fail(SCL_E_TIMEOUT, "a bounded device wait gave up");
     if (ctx->h_result->status == SCL_E_STATE)
         return fail(SCL_E_STATE, "the keys changed while the call read them");
     if (ctx->h_result->status == SCL_E_KEY_RANGE)

@@ -839,9 +839,11 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
             r->f32_min = CUDART_INF_F;
             r->f32_max = -CUDART_INF_F;
             // bit 0: a key out of range; bit 1: the bucket-partitioned path
-            // counted the keys differently in its two reads (they changed)
+            // counted the keys differently in its two reads (they changed);
+            // bit 2: one of its bounded waits ran out
             const uint32_t bad = __ldcg(a.bad);
-            r->status = (bad & 2u) ? SCL_E_STATE : bad ? SCL_E_KEY_RANGE : SCL_OK;
+            r->status = (bad & 4u) ? SCL_E_TIMEOUT
+                        : (bad & 2u) ? SCL_E_STATE : bad ? SCL_E_KEY_RANGE : SCL_OK;
             r->n = a.n;
             r->kind = K_KEYED;
             *a.ticket = 0u;

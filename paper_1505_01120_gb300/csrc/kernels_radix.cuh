@@ -9,6 +9,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "kernels_tma.cuh"
 #include "radix.h"
 
 namespace scl {
@@ -202,24 +203,35 @@ __global__ void __launch_bounds__(BLOCK) k_radix_scan(const __grid_constant__ Ra
 
 // Pass 3: per tile, (HOT) pairs of hot ids into the CTA's hot table, and for
 // the others ranks within buckets, tile offsets, the pairs grouped in shared
-// memory, then written out as runs.  The next tile's loads are issued
-// before the write-out.  Offsets inside a chunk are 32-bit (n < 2^31).  Three
-// CTAs per SM (at most 40 registers) keep loads in flight across the tile's
-// barriers.
-template <int BLOCK, int LOG_T, bool HOT>
+// memory, then written out as runs.  Offsets inside a chunk are 32-bit
+// (n < 2^31).  The next tile's keys and values are fetched while this one
+// is ranked, grouped and written: with TMA, by two bulk copies into a shared
+// input buffer issued as soon as the ranks are taken (its mbarrier wait is
+// bounded; a wait that runs out sets kRadixBadWait and the CTA stops after
+// waiting, bounded, for its copies); otherwise by register loads issued
+// before the write-out.  Three CTAs per SM (at most 40 registers) where the
+// shared memory allows.
+template <int BLOCK, int LOG_T, bool HOT, bool TMA>
 __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constant__ RadixArgs a) {
     // both forms are launched; the scan's choice runs, the other returns
     if (__ldcg(a.mode) != (HOT ? 1u : 0u)) return;
     static_assert(BLOCK * 8 == (int)kRadixTile && 2 * BLOCK == (int)kRadixMaxBuckets, "tile");
+    static_assert(TMA == radix_scatter_tma(HOT), "the form's layout is radix_scatter_smem's");
     constexpr int W = BLOCK / 32;
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint2* stage = reinterpret_cast<uint2*>(smem);   // [kRadixTile]
-    uint32_t* hcnt = smem + 2 * kRadixTile;          // [kRadixHotIds] hot counts
+    constexpr uint32_t IN_W = radix_scatter_in_words(TMA);
+    constexpr uint32_t HOT_W = radix_scatter_hot_words(HOT);
+    extern __shared__ __align__(16) uint32_t rsmem[];
+    uint32_t* smem = rsmem;
+    const uint32_t* in_k = smem;                       // TMA: [kRadixTile] keys
+    const uint32_t* in_v = smem + kRadixTile;          // TMA: [kRadixTile] values
+    const uint32_t bar = smem_u32(smem + 2 * kRadixTile);   // TMA: the input mbarrier
+    uint2* stage = reinterpret_cast<uint2*>(smem + IN_W);   // [kRadixTile]
+    uint32_t* hcnt = smem + IN_W + 2 * kRadixTile;     // HOT: [kRadixHotIds] hot counts
     float* hsum = reinterpret_cast<float*>(hcnt + kRadixHotIds);   // [kRadixHotIds]
-    float* heads = hsum + kRadixHotIds;              // head copies of ids < kKeyedHead
+    float* heads = hsum + kRadixHotIds;                // head copies of ids < kKeyedHead
     float* myhead = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
                              (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
-    uint32_t* tcnt = smem + kRadixScatterFixedWords; // [nb] pairs of the tile
+    uint32_t* tcnt = smem + IN_W + 2 * kRadixTile + HOT_W;   // [nb] pairs of the tile
     uint32_t* toff = tcnt + a.nb;                    // [nb] their first slot in the tile
     uint32_t* shift = toff + a.nb;                   // [nb] bk position - tile slot
     uint32_t* gcur = shift + a.nb;                   // [nb] next position in bk
@@ -230,8 +242,20 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
     uint2* bk = reinterpret_cast<uint2*>(a.bk);
     uint32_t bad = 0;
     if (HOT)
-        for (uint32_t i = threadIdx.x; i < 2 * kRadixHotIds + kKeyedHeadWords(BLOCK); i += BLOCK)
+        for (uint32_t i = threadIdx.x; i < HOT_W; i += BLOCK)
             hcnt[i] = 0u;   // hot counts, sums and head copies
+    uint32_t phase = 0;   // TMA: parity of the input mbarrier's next phase
+    if (TMA && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // TMA, thread 0: the whole tile at t0 of the chunk into the input buffer
+    auto issue = [&](const char* kp, const char* vp, uint32_t t0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_tx(bar, 2 * kRadixTile * 4);
+        bulk_g2s(smem_u32(in_k), kp + (size_t)t0 * 4, kRadixTile * 4, bar);
+        bulk_g2s(smem_u32(in_v), vp + (size_t)t0 * 4, kRadixTile * 4, bar);
+    };
     // hot table -> outputs (global atomics), cleared; between barriers
     auto flush_hot = [&]() {
         fold_head_copies(heads, hsum, kKeyedHead);
@@ -248,7 +272,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
         __syncthreads();
     };
     uint32_t tiles = 0;   // since the hot table's last flush
-    for (uint32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
+    bool stopped = false;
+    for (uint32_t c = blockIdx.x; c < a.nchunks && !stopped; c += gridDim.x) {
         for (uint32_t i = threadIdx.x; i < nb; i += BLOCK) {
             // without the bypass bucket 0 holds the hot ids too (row nb)
             gcur[i] = a.bstart[i] + a.hist[(size_t)i * a.nchunks + c] +
@@ -261,6 +286,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
         const char* vp = a.vals + b0 * 4;
         uint4 kk[2], vv[2];
         uint32_t in[2];
+        // register loads of the tile at t0 (every tile without TMA, the ragged
+        // last tile with it)
         auto load = [&](uint32_t t0) {
             if (t0 + kRadixTile <= len) {   // CTA-uniform: a whole tile
 #pragma unroll
@@ -280,9 +307,29 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
                 }
             }
         };
-        load(0);
+        if (TMA) {
+            if (threadIdx.x == 0 && kRadixTile <= len) issue(kp, vp, 0);
+        } else {
+            load(0);
+        }
         __syncthreads();
         for (uint32_t t0 = 0; t0 < len; t0 += kRadixTile) {
+            bool ok = true;
+            if (TMA) {
+                if (t0 + kRadixTile <= len) {   // CTA-uniform: the bulk-copied tile
+                    ok = mbar_wait(bar, phase, a.bad);
+                    phase ^= 1u;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t i = ((uint32_t)j * BLOCK + threadIdx.x) * 4;
+                        kk[j] = ok ? *reinterpret_cast<const uint4*>(in_k + i) : make_uint4(0, 0, 0, 0);
+                        vv[j] = ok ? *reinterpret_cast<const uint4*>(in_v + i) : make_uint4(0, 0, 0, 0);
+                        in[j] = ok ? 0xfu : 0u;   // after a failed wait: no pairs
+                    }
+                } else {
+                    load(t0);
+                }
+            }
             const uint32_t k[8] = {kk[0].x, kk[0].y, kk[0].z, kk[0].w,
                                    kk[1].x, kk[1].y, kk[1].z, kk[1].w};
             const uint32_t v[8] = {vv[0].x, vv[0].y, vv[0].z, vv[0].w,
@@ -297,12 +344,25 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
                     atomicAdd(k[q] < kKeyedHead ? &myhead[k[q]] : &hsum[k[q]],
                               __uint_as_float(v[q]));
                 }
-                const bool ok = in_range && (!HOT || k[q] >= kRadixHotIds);
-                valid |= ok ? 1u << q : 0u;
-                const uint32_t r = warp_rank(tcnt, ok ? k[q] >> lt : kNoBucket, lane);
+                const bool cold = in_range && (!HOT || k[q] >= kRadixHotIds);
+                valid |= cold ? 1u << q : 0u;
+                const uint32_t r = warp_rank(tcnt, cold ? k[q] >> lt : kNoBucket, lane);
                 rank2[q >> 1] |= (r & 0xffffu) << (16 * (q & 1));
             }
-            __syncthreads();
+            if (TMA) {
+                if (__syncthreads_or(!ok)) {   // a wait ran out: stop this CTA
+                    if (threadIdx.x == 0) {
+                        mbar_wait(bar, phase ^ 1u, a.bad);   // its copy, bounded
+                        atomicOr(a.bad, kRadixBadWait);
+                    }
+                    stopped = true;
+                    break;
+                }
+                // the input buffer is read: fetch the next whole tile into it
+                if (threadIdx.x == 0 && t0 + 2 * kRadixTile <= len) issue(kp, vp, t0 + kRadixTile);
+            } else {
+                __syncthreads();
+            }
             // tile offsets: buckets 2t and 2t + 1 in thread t (nb <= 2 * BLOCK)
             const uint32_t b2 = 2 * threadIdx.x;
             uint32_t x = (b2 < nb ? tcnt[b2] : 0u) + (b2 + 1 < nb ? tcnt[b2 + 1] : 0u);
@@ -343,7 +403,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
                 }
             const uint32_t tn = min(wsum[W], kRadixTile);
             __syncthreads();
-            if (t0 + kRadixTile < len) load(t0 + kRadixTile);
+            if (!TMA && t0 + kRadixTile < len) load(t0 + kRadixTile);
             for (uint32_t i = threadIdx.x; i < tn; i += BLOCK) {
                 const uint2 p = stage[i];
                 const uint32_t pb = p.x >> lt;
@@ -351,7 +411,6 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
                 if (pos < cap) bk[pos] = make_uint2(p.x & idmask, p.y);
                 else bad = kRadixBadPlace;
             }
-
             // No barrier here: the next tile rewrites stage, toff, shift and
             // wsum only after the barrier that follows its ranks, which every
             // thread reaches after this write-out.
@@ -362,7 +421,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
         }
         __syncthreads();   // gcur and tcnt are reset for the next chunk
     }
-    if (HOT && tiles) flush_hot();
+    if (HOT && tiles && !stopped) flush_hot();
     if (bad) atomicOr(a.bad, bad);
 }
 
@@ -376,7 +435,8 @@ template <int BLOCK, int LOG_T>
 __global__ void __launch_bounds__(BLOCK) k_radix_reduce(const __grid_constant__ RadixArgs a) {
     constexpr uint32_t T = 1u << LOG_T;
     constexpr uint32_t HP = kKeyedHeadStride;
-    extern __shared__ __align__(16) uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t rsmem[];
+    uint32_t* smem = rsmem;
     uint32_t* hc = smem;                                   // [T] counts
     float* hs = reinterpret_cast<float*>(smem + T);        // [T] fp32 sums
     float* head = hs + T;                                  // [BLOCK / 32 * classes][HP]

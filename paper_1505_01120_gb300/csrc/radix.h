@@ -50,7 +50,8 @@ constexpr uint32_t kRadixChunkAlign = kRadixHistTile;    // chunk lengths, in pa
 constexpr uint64_t kRadixMinPairs = 1u << 20;            // smaller partitions: direct path
 constexpr uint64_t kRadixMaxPairs = (1ull << 31) - 1;    // offsets are uint32
 constexpr uint32_t kRadixBadKey = 1u;                    // flag bit: key out of range
-constexpr uint32_t kRadixBadPlace = 2u;                  // flag bit: pass 2 saw other counts
+constexpr uint32_t kRadixBadPlace = 2u;                  // flag bit: pass 3 saw other counts
+constexpr uint32_t kRadixBadWait = 4u;                   // flag bit: a bounded wait ran out
 constexpr uint32_t kRadixScanBlock = 256;                // 8 bucket rows per CTA
 constexpr uint32_t kRadixMaxBuckets = 2 * kRadixBlock;   // two per scatter thread
 constexpr uint32_t kRadixPreferredBuckets = 256;         // runs of 16 pairs per tile
@@ -114,15 +115,28 @@ __host__ __device__ inline RadixLayout radix_layout(uint64_t n, const RadixGeome
     return l;
 }
 
-// Dynamic shared memory of the scatter kernel, in words: the tile, the hot
-// table (counts, fp32 sums, head copies), then count / tile offset / shift /
-// cursor words per bucket, then one word per warp and the tile total.
-constexpr uint32_t kRadixScatterFixedWords =
-    2 * kRadixTile + 2 * kRadixHotIds + kKeyedHeadWords(kRadixBlock);
-__host__ __device__ inline uint32_t radix_hist_smem(uint32_t nb) { return (nb + 1) * 4; }
-__host__ __device__ inline uint32_t radix_scatter_smem(uint32_t nb) {
-    return (kRadixScatterFixedWords + 4 * nb + kRadixBlock / 32 + 4) * 4;
+// Dynamic shared memory of the scatter kernel, in words: (TMA) the input
+// tile -- keys, values -- and its mbarrier, the stage tile, (HOT) the hot
+// table -- counts, fp32 sums, head copies --, then count / tile offset /
+// shift / cursor words per bucket, then one word per warp and the tile total.
+__host__ __device__ constexpr uint32_t radix_scatter_in_words(bool tma) {
+    return tma ? 2 * kRadixTile + 4 : 0u;
 }
+__host__ __device__ constexpr uint32_t radix_scatter_hot_words(bool hot) {
+    return hot ? 2 * kRadixHotIds + kKeyedHeadWords(kRadixBlock) : 0u;
+}
+// Whether a form stages its input with TMA: the plain one.  (Measured on
+// GB300, 64 Mi pairs: the plain form 5-6% faster with it at 3 CTAs per SM;
+// the hot-id form, at 2 CTAs per SM with it, 2-3% slower.)
+__host__ __device__ constexpr bool radix_scatter_tma(bool hot) { return !hot; }
+__host__ __device__ inline uint32_t radix_scatter_smem(uint32_t nb, bool hot) {
+    return (radix_scatter_in_words(radix_scatter_tma(hot)) + 2 * kRadixTile +
+            radix_scatter_hot_words(hot) + 4 * nb + kRadixBlock / 32 + 4) * 4;
+}
+
+// Dynamic shared memory of the histogram kernel: a count per bucket and the
+// hot row.
+__host__ __device__ inline uint32_t radix_hist_smem(uint32_t nb) { return (nb + 1) * 4; }
 
 // The reduce kernel per bucket width: threads per CTA and dynamic shared
 // memory (count and fp32 sum per id, then the head copies).

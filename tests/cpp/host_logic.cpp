@@ -203,8 +203,9 @@ static void check_radix() {
         CHECK(l.tot >= l.hist + (uint64_t)g.nb * g.nchunks * 4 && l.bstart >= l.tot + g.nb * 4ull &&
                   l.total >= l.bstart + (g.nb + 1ull) * 4,
               "tables overlap");
-        CHECK(radix_scatter_smem(g.nb) <= 227 * 1024, "scatter shared memory %u",
-              radix_scatter_smem(g.nb));
+        for (int hot = 0; hot < 2; ++hot)
+            CHECK(radix_scatter_smem(g.nb, hot != 0) <= 227 * 1024,
+                  "scatter shared memory %u", radix_scatter_smem(g.nb, hot != 0));
     }
     // replay of the passes' offsets (scaled-down sizes, same formulas)
     for (int it = 0; it < 48; ++it) {
