@@ -8,7 +8,9 @@
 // kRadixPreferredBuckets, so that a tile of the scatter writes runs of
 // several pairs per bucket (on GB300 the scatter took 288 / 401 / 600 us for
 // 64 Mi pairs into 256 / 512 / 1024 buckets, more than a wider table costs
-// the reduce); above 2^22 keys, 16384-id buckets (up to 1024).
+// the reduce; the whole call over 2^20 uniform keys took 506 / 481 / 486 us
+// preferring 256 / 128 / 64 buckets); above 2^21 keys, 16384-id buckets (up
+// to 1024).
 // Ids below kRadixHotIds -- the frequent words when a vocabulary is numbered
 // by frequency -- are counted apart by the histogram; when they hold at
 // least 1/8 of the pairs they are not partitioned: the scatter counts them in
@@ -54,7 +56,7 @@ constexpr uint32_t kRadixBadPlace = 2u;                  // flag bit: pass 3 saw
 constexpr uint32_t kRadixBadWait = 4u;                   // flag bit: a bounded wait ran out
 constexpr uint32_t kRadixScanBlock = 256;                // 8 bucket rows per CTA
 constexpr uint32_t kRadixMaxBuckets = 2 * kRadixBlock;   // two per scatter thread
-constexpr uint32_t kRadixPreferredBuckets = 256;         // runs of 16 pairs per tile
+constexpr uint32_t kRadixPreferredBuckets = 128;         // runs of 32 pairs per tile
 constexpr uint32_t kRadixHotIds = 1024;                  // ids kept out of the partition
 constexpr uint32_t kRadixHotFlushTiles = 32;             // kLargePiece pairs
 constexpr uint32_t kRadixMinLogT = 12;                   // 4096 ids per bucket

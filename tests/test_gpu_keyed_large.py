@@ -167,10 +167,13 @@ RADIX_CASES = {
     # buckets per thread in the tile scan)
     "wide_buckets": lambda rng: ((1 << 23) + 1,
                                  rng.integers(0, (1 << 23) + 1, (1 << 20) + 5, dtype=np.int32)),
+    # 2^19 + 3 keys: 65 buckets of 8192 ids, the last holding 3
+    "buckets_8192": lambda rng: ((1 << 19) + 3,
+                                 rng.integers(0, (1 << 19) + 3, (1 << 20) + 11, dtype=np.int32)),
     # 2^22 keys: 256 buckets of 16384 ids
     "mid_buckets": lambda rng: (1 << 22, rng.integers(0, 1 << 22, 3 << 20, dtype=np.int32)),
-    # 2^21 + 7 keys: 257 buckets of 8192 ids, the last holding 7
-    "buckets_8192": lambda rng: ((1 << 21) + 7,
+    # 2^21 + 7 keys: 129 buckets of 16384 ids, the last holding 7
+    "buckets_16384": lambda rng: ((1 << 21) + 7,
                                  rng.integers(0, (1 << 21) + 7, (1 << 21) + 3, dtype=np.int32)),
     # sorted keys: CTAs that hold whole buckets store them without atomics
     "sorted": lambda rng: (1 << 22, np.sort(rng.integers(0, 1 << 22, 1 << 21,
