@@ -25,7 +25,7 @@ const void* radix_scatter_fn(uint32_t log_t, bool hot) {
 const void* radix_reduce_fn(uint32_t log_t) {
     switch (log_t) {
         case 12: return (const void*)&dev::k_radix_reduce<512, 12>;
-        case 13: return (const void*)&dev::k_radix_reduce<512, 13>;
+        case 13: return (const void*)&dev::k_radix_reduce<1024, 13>;
         case 14: return (const void*)&dev::k_radix_reduce<1024, 14>;
         default: return nullptr;
     }

@@ -142,8 +142,9 @@ __host__ __device__ inline uint32_t radix_hist_smem(uint32_t nb) { return (nb + 
 
 // The reduce kernel per bucket width: threads per CTA and dynamic shared
 // memory (count and fp32 sum per id, then the head copies).
+// (8192 ids: 2 CTAs of 1024 threads per SM beat 3 of 512 by 3% on GB300.)
 __host__ __device__ inline uint32_t radix_reduce_block(uint32_t log_t) {
-    return log_t >= 14 ? 1024u : 512u;
+    return log_t >= 13 ? 1024u : 512u;
 }
 __host__ __device__ inline uint32_t radix_reduce_smem(uint32_t log_t) {
     return ((2u << log_t) + kKeyedHeadWords(radix_reduce_block(log_t))) * 4;
