@@ -119,8 +119,9 @@ typedef struct {
  *                         (NaN ignored; empty: +inf / -inf)
  *   KEYED_COUNT_SUM:      u64_sum = pairs counted, f64_sum = their value sum
  *   n:                    elements (pairs) in the partition
- *   status:               SCL_OK or SCL_E_KEY_RANGE (SCL_E_STATE: the
- *                         large-key reduce saw its keys change)            */
+ *   status:               SCL_OK or SCL_E_KEY_RANGE (the large-key reduce
+ *                         also: SCL_E_STATE, its keys changed;
+ *                         SCL_E_TIMEOUT, a bounded device wait ran out)     */
 typedef struct {
     uint64_t u64_sum;
     double f64_sum;
@@ -313,7 +314,8 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
  * tables from the arena (16 B per key), released before returning.  Returns
  * SCL_E_KEY_RANGE after writing the valid pairs' tables if a key was outside
  * [0, num_keys); SCL_E_STATE if the keys changed while the call read them
- * (the partitioned path reads them twice). */
+ * (the partitioned path reads them twice); SCL_E_TIMEOUT if one of the
+ * partitioned path's bounded waits for its bulk copies ran out. */
 int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
                            uint32_t* counts_out, float* sums_out, double* sums64_out,
                            scl_result* result);
