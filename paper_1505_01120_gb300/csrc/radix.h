@@ -101,7 +101,7 @@ struct RadixLayout {
 // keys over 2^24 ids (1023 buckets of ~650 pairs beside one of 60 Mi): a
 // quarter of the ids left the last CTAs with the small buckets (972 us), the
 // full count balanced them (771 us), twice it over-corrected (820 us).
-__host__ __device__ inline uint32_t radix_bucket_cost(uint32_t log_t) { return 1u << log_t; }
+__host__ __device__ constexpr uint32_t radix_bucket_cost(uint32_t log_t) { return 1u << log_t; }
 
 __host__ __device__ inline uint64_t radix_up256(uint64_t x) { return (x + 255) / 256 * 256; }
 
@@ -131,7 +131,7 @@ __host__ __device__ constexpr uint32_t radix_scatter_hot_words(bool hot) {
 // GB300, 64 Mi pairs: the plain form 5-6% faster with it at 3 CTAs per SM;
 // the hot-id form, at 2 CTAs per SM with it, 2-3% slower.)
 __host__ __device__ constexpr bool radix_scatter_tma(bool hot) { return !hot; }
-__host__ __device__ inline uint32_t radix_scatter_smem(uint32_t nb, bool hot) {
+__host__ __device__ constexpr uint32_t radix_scatter_smem(uint32_t nb, bool hot) {
     return (radix_scatter_in_words(radix_scatter_tma(hot)) + 2 * kRadixTile +
             radix_scatter_hot_words(hot) + 4 * nb + kRadixBlock / 32 + 4) * 4;
 }
@@ -143,12 +143,23 @@ __host__ __device__ inline uint32_t radix_hist_smem(uint32_t nb) { return (nb + 
 // The reduce kernel per bucket width: threads per CTA and dynamic shared
 // memory (count and fp32 sum per id, then the head copies).
 // (8192 ids: 2 CTAs of 1024 threads per SM beat 3 of 512 by 3% on GB300.)
-__host__ __device__ inline uint32_t radix_reduce_block(uint32_t log_t) {
+__host__ __device__ constexpr uint32_t radix_reduce_block(uint32_t log_t) {
     return log_t >= 13 ? 1024u : 512u;
 }
-__host__ __device__ inline uint32_t radix_reduce_smem(uint32_t log_t) {
+__host__ __device__ constexpr uint32_t radix_reduce_smem(uint32_t log_t) {
     return ((2u << log_t) + kKeyedHeadWords(radix_reduce_block(log_t))) * 4;
 }
+
+// Limits the kernels rely on: cost starts fit 32 bits at the largest
+// partition and bucket count, and every form's shared memory fits a CTA.
+static_assert((uint64_t)kRadixMaxPairs +
+                      (uint64_t)kRadixMaxBuckets * radix_bucket_cost(kRadixMaxLogT) <
+                  (1ull << 32),
+              "cost starts overflow");
+static_assert(radix_scatter_smem(kRadixMaxBuckets, false) <= 227 * 1024 &&
+                  radix_scatter_smem(kRadixMaxBuckets, true) <= 227 * 1024,
+              "scatter shared memory");
+static_assert(radix_reduce_smem(kRadixMaxLogT) <= 227 * 1024, "reduce shared memory");
 
 struct RadixArgs {
     const char* keys;         // int32 keys, 16-byte aligned
