@@ -10,7 +10,9 @@
 //     and, replaying the four passes' offset arithmetic on random keys, that
 //     every partitioned pair is written once inside its bucket and read once
 //     by the reduce's cost shares (hot ids counted apart), with no index
-//     outside the tables and no share far above its cost.
+//     outside the tables and no share far above its cost;
+//   * the scatter's TMA form: every bulk copy it issues is waited on exactly
+//     once, in order, with never two outstanding.
 // Prints "ok" and exits 0, or names the first failed check and exits 1.
 #include <stdio.h>
 #include <stdlib.h>
@@ -340,12 +342,54 @@ static void check_radix() {
     }
 }
 
+// The large-key scatter's TMA form (plain form): one input buffer, one
+// mbarrier.  Replays a CTA's issue / wait sequence over its chunks: the first
+// whole tile of a chunk is issued at the chunk's start, the next whole tile
+// right after a tile's ranks; a whole tile waits on the barrier, a ragged
+// last tile loads by registers.  Every issued copy must be waited on exactly
+// once, in order (phase parity alternating), and no copy may be issued while
+// another is outstanding (the buffer is single).
+static void check_radix_tma_protocol() {
+    std::mt19937_64 rng(6);
+    for (int it = 0; it < 20000; ++it) {
+        const uint32_t nchunks = 1 + (uint32_t)(rng() % 5);
+        uint32_t issued = 0, waited = 0, phase = 0;
+        bool outstanding = false;
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint32_t len = it < 64 ? (uint32_t)(it * 1024)
+                                         : (uint32_t)(rng() % (12 * kRadixTile + 3));
+            if (kRadixTile <= len) {   // chunk start
+                CHECK(!outstanding, "issue while a copy is outstanding (chunk start)");
+                outstanding = true;
+                ++issued;
+            }
+            for (uint32_t t0 = 0; t0 < len; t0 += kRadixTile) {
+                if (t0 + kRadixTile <= len) {   // whole tile: wait on the barrier
+                    CHECK(outstanding, "wait with no copy issued (len %u, t0 %u)", len, t0);
+                    outstanding = false;
+                    ++waited;
+                    phase ^= 1u;
+                }
+                // after the ranks: the next whole tile
+                if (t0 + 2 * kRadixTile <= len) {
+                    CHECK(!outstanding, "issue while a copy is outstanding (len %u)", len);
+                    outstanding = true;
+                    ++issued;
+                }
+            }
+        }
+        CHECK(!outstanding && issued == waited, "copies issued %u, waited %u", issued, waited);
+        CHECK(phase == (waited & 1u), "phase parity");
+    }
+}
+
 int main() {
     check_stream_segments();
     if (!g_fail) check_keyed_single();
     if (!g_fail) check_keyed_plan();
     if (!g_fail) check_range_alloc();
     if (!g_fail) check_radix();
+    if (!g_fail) check_radix_tma_protocol();
     if (g_fail) return 1;
     printf("ok\n");
     return 0;

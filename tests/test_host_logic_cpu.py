@@ -1,6 +1,6 @@
 """Host-side logic of the library, without a GPU: segment geometry, keyed
-piece planning, the range allocator and the bucket-partitioned large-key
-reduce's offsets (tests/cpp/host_logic.cpp, built with
+piece planning, the range allocator, and the bucket-partitioned large-key
+reduce's offsets and bulk-copy protocol (tests/cpp/host_logic.cpp, built with
 the host C++ compiler from the library's own headers)."""
 from __future__ import annotations
 
