@@ -489,10 +489,10 @@ int scl_batch_run(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
 /* Map + reduce of one partition without allocating anything: no context, no
  * arena, no cudaMalloc/cudaFree, no pinned staging, no allocating library
  * call.  The paper has no counterpart; this exists for callers that cannot
- * allocate device memory at the moment they need a result -- code running
- * while a CUDA stream capture is open, plug-ins inside an application whose
- * own pool already holds all of the GPU's memory, and latency-critical paths
- * that cannot take the device synchronisation of cudaMalloc/cudaFree.
+ * allocate device memory at the moment they need a result -- plug-ins inside
+ * an application whose own pool already holds all of the GPU's memory, and
+ * latency-critical paths that cannot take the device synchronisation of
+ * cudaMalloc/cudaFree.
  *
  * dev_in: device array of n elements of `dtype` (U32, I32 or F32; 4-byte
  * aligned, 16-byte aligned takes the vector path).  kernel / coef / reduce:
@@ -500,14 +500,16 @@ int scl_batch_run(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
  * written when `stream` reaches the launch.  Enqueue-only: nothing is
  * synchronised.
  *
- * Scratch: a fixed device array of 256 B of counters plus 4096 segment
- * partials of 32 B (about 128 KB) inside the library; every GPU that loads the
+ * Scratch: a fixed device array inside the library, 96 B of counters plus
+ * 4096 segment partials of 32 B (128 KB in all); every GPU that loads the
  * library holds it until the process exits.  Partitions larger than
  * SCL_NOALLOC_MAX_ELEMENTS are rejected with SCL_E_INVALID before anything is
  * enqueued.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) and the launch limits, with that device current;
- * make that first call before any stream capture.  Each call clears the
- * counters it needs on `stream` before its launch.  All calls share the one
+ * (cudaGetSymbolAddress) and the launch limits, with that device current,
+ * and keeps them for that device ordinal for the life of the process (a
+ * cudaDeviceReset is not followed); make that first call before any stream
+ * capture.  Each call clears the 96 B of counters on `stream` before its
+ * launch.  All calls share the one
  * array: calls whose work can overlap on the GPU (different streams, or
  * different host threads) race and give wrong results -- order them, e.g. on
  * one stream.  Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED, SCL_E_CUDA. */

@@ -139,7 +139,7 @@ struct KernelArgs {
 };
 
 // Geometry of a streaming task's segments, shared by host planning and tests.
-__host__ __device__ inline uint32_t stream_seg_elems(uint64_t n, uint32_t chunk) {
+__host__ __device__ constexpr uint32_t stream_seg_elems(uint64_t n, uint32_t chunk) {
     uint64_t per = (uint64_t)chunk * kTargetSegsPerTask;
     uint64_t c = (n + per - 1) / per;
     if (c < 1) c = 1;
@@ -147,7 +147,7 @@ __host__ __device__ inline uint32_t stream_seg_elems(uint64_t n, uint32_t chunk)
     return (uint32_t)(c * chunk);
 }
 
-__host__ __device__ inline uint32_t stream_nseg(uint64_t n, uint32_t seg_elems) {
+__host__ __device__ constexpr uint32_t stream_nseg(uint64_t n, uint32_t seg_elems) {
     uint64_t s = (n + seg_elems - 1) / seg_elems;
     return s < 1 ? 1u : (uint32_t)s;
 }

@@ -1,11 +1,9 @@
 // noalloc.cu -- a map+reduce entry point that allocates no memory at all.
 //
-// Some callers cannot allocate device memory when they need a result: code
-// running while a CUDA stream capture is open (cudaMalloc is not allowed
-// then), plug-ins living inside a host application that has already claimed
-// all of the GPU's memory through its own pool, and latency-critical paths
-// that cannot afford the implicit device synchronisation of cudaMalloc /
-// cudaFree.  scl_map_reduce_noalloc serves them: it needs no context, no
+// Some callers cannot allocate device memory when they need a result:
+// plug-ins living inside a host application that has already claimed all of
+// the GPU's memory through its own pool, and latency-critical paths that
+// cannot afford the implicit device synchronisation of cudaMalloc / cudaFree.  scl_map_reduce_noalloc serves them: it needs no context, no
 // arena and no pinned staging buffer.  The caller passes the input array and
 // a device scl_result slot; the only scratch is the file-scope device array
 // below, which every GPU that loads the library keeps until the process exits.
@@ -40,6 +38,13 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
+// The largest accepted partition must fit the partial slots at the launch shape.
+static_assert(stream_nseg(SCL_NOALLOC_MAX_ELEMENTS,
+                          stream_seg_elems(SCL_NOALLOC_MAX_ELEMENTS, kNaBlock * kNaIpt * 4)) <=
+                  kNaMaxSegments,
+              "SCL_NOALLOC_MAX_ELEMENTS exceeds the scratch's segment partials");
+static_assert(offsetof(NoAllocScratch, part) == 96, "counters cleared per call: 96 bytes");
+
 struct DeviceSetup {
     bool ready = false;
     NoAllocScratch* scratch = nullptr;   // device address of g_noalloc_scratch
@@ -52,7 +57,9 @@ DeviceSetup g_setup[kNaMaxDevices];
 
 // Once per device, with that device current: resolve the array's device
 // address (host code only ever sees a host-side stand-in for the symbol) and
-// the launch limits.
+// the launch limits.  The cache is per device ordinal: it assumes the
+// device's primary context lives as long as the library (a cudaDeviceReset,
+// or a caller's own driver-API context, would need the lookup again).
 int setup_device(int dev, DeviceSetup** out) {
     std::lock_guard<std::mutex> g(g_setup_mu);
     DeviceSetup& s = g_setup[dev];

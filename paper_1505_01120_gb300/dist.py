@@ -60,16 +60,36 @@ def combine_across_ranks(results: np.ndarray, group=None):
 
 
 def combine_keyed_across_ranks(counts: np.ndarray, sums64: np.ndarray, group=None):
-    """Merge keyed tables [k_local, num_keys] of every rank into one table:
-    the library's host merge of the local tables, then one sum across ranks
-    (counts exact in int64, sums in fp64)."""
+    """ReduceCL over the keyed tables of every rank: each rank's tables
+    [k_local, num_keys] (count uint32, sum fp64) are all-gathered as bytes,
+    then folded by the library's host merge, scl_combine_keyed, in rank order
+    (counts exact, sums in fp64).  Returns (counts, sums64) on every rank."""
     import torch
     import torch.distributed as dist
     from . import scl
-    lc, ls = scl.scl_combine_keyed(np.ascontiguousarray(counts, np.uint32),
-                                   np.ascontiguousarray(sums64, np.float64))
-    tc = torch.from_numpy(lc.astype(np.int64))
-    ts = torch.from_numpy(ls.copy())
-    dist.all_reduce(tc, group=group)
-    dist.all_reduce(ts, group=group)
-    return tc.numpy().astype(np.uint32), ts.numpy()
+    counts = np.ascontiguousarray(np.atleast_2d(counts), np.uint32)
+    sums64 = np.ascontiguousarray(np.atleast_2d(sums64), np.float64)
+    k, nk = counts.shape
+    if sums64.shape != (k, nk):
+        raise ValueError("counts and sums64 must have the same shape")
+    world = dist.get_world_size(group)
+    rows = torch.tensor([k, nk], dtype=torch.int64)
+    got = [torch.zeros(2, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(got, rows, group=group)
+    if any(int(g[1]) != nk for g in got):
+        raise ValueError("ranks disagree on num_keys")
+    kmax = max(int(g[0]) for g in got)
+    pack = np.zeros((max(kmax, 1), nk * 12), np.uint8)   # per row: counts, then sums
+    pack[:k, :nk * 4] = counts.view(np.uint8).reshape(k, nk * 4)
+    pack[:k, nk * 4:] = sums64.view(np.uint8).reshape(k, nk * 8)
+    bufs = [torch.zeros(pack.shape, dtype=torch.uint8) for _ in range(world)]
+    dist.all_gather(bufs, torch.from_numpy(pack), group=group)
+    cs, ss = [], []
+    for b, g in zip(bufs, got):
+        rows_r = b.numpy()[:int(g[0])]
+        cs.append(np.ascontiguousarray(rows_r[:, :nk * 4]).view(np.uint32).reshape(-1, nk))
+        ss.append(np.ascontiguousarray(rows_r[:, nk * 4:]).view(np.float64).reshape(-1, nk))
+    allc, alls = np.concatenate(cs), np.concatenate(ss)
+    if allc.shape[0] == 0:
+        return np.zeros(nk, np.uint32), np.zeros(nk, np.float64)
+    return scl.scl_combine_keyed(allc, alls)

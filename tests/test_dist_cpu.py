@@ -57,8 +57,11 @@ def _worker(rank, world, port, q, mode):
         r = sdist.combine_across_ranks(res)
         keys = (np.arange(5000) % 64).astype(np.int32) + rank
         vals = np.full(5000, 0.5 + rank, np.float32)
-        cnt, s64, _ = oracle.keyed_count_sum(keys, vals, 128)
-        kc, ks = sdist.combine_keyed_across_ranks(cnt[None, :], s64[None, :])
+        # rank 0 holds two partition tables, rank 1 one: uneven row counts
+        cuts = [0, 2000, 5000] if rank == 0 else [0, 5000]
+        tabs = [oracle.keyed_count_sum(keys[a:b], vals[a:b], 128) for a, b in zip(cuts, cuts[1:])]
+        kc, ks = sdist.combine_keyed_across_ranks(np.stack([t[0] for t in tabs]),
+                                                  np.stack([t[1] for t in tabs]))
         q.put((rank, (mine, r.u64_sum, r.f64_sum, r.f32_min, r.f32_max, r.n, kc, ks)))
     except Exception as e:   # the surviving rank reports the failed merge
         q.put((rank, "error: %s" % type(e).__name__))

@@ -48,8 +48,7 @@ def test_library_exports_every_declared_symbol(scl):
         assert hasattr(scl.lib, name)
     # the binding wraps every declared function
     assert decl <= set(scl.exported_symbols()) | {"scl_server_stop"} | \
-        {n for n in decl if n.startswith("scl_server") or n.startswith("scl_tune")
-         or n.startswith("scl_noalloc")}
+        {n for n in decl if n.startswith("scl_server") or n.startswith("scl_tune")}
 
 
 def test_struct_layouts_match_header(scl):
