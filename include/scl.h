@@ -196,6 +196,14 @@ int scl_load_partition(scl_ctx* ctx, const void* host, scl_dtype dtype,
 int scl_load_partition_kv(scl_ctx* ctx, const int32_t* keys, const float* vals,
                           uint64_t n, void* stream, scl_part* out);
 
+/* mapParameters for data produced on the device (Sec. 3.1.1.1): a new
+ * arena-resident partition of n elements of `dtype` (keyed: keys then values)
+ * whose contents are undefined until the caller writes them through the
+ * device pointers scl_partition_info returns.  Nothing is copied or enqueued.
+ * Like a loaded partition it is library-owned and counts as resident data in
+ * the servers' HBM budget.  Errors: SCL_E_INVALID (bad dtype), SCL_E_NOMEM. */
+int scl_alloc_partition(scl_ctx* ctx, scl_dtype dtype, uint64_t n, scl_part* out);
+
 /* Wrap caller-owned device arrays as a partition without copying (e.g. a
  * torch tensor's data_ptr).  dev1 is the value array for SCL_KV_I32_F32 and
  * must be NULL otherwise.  The arrays must outlive the handle.  4-byte
@@ -585,6 +593,26 @@ int scl_server_stop(scl_ctx* ctx);
  * results[i] the result (may be NULL).  Runs on the calling thread. */
 int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s,
                       uint32_t n, int64_t* latency_ns, scl_result* results);
+
+/* Data of one task of a replayed trace that brings new data
+ * (scl_server_replay_load): host0[n] (keys for SCL_KV_I32_F32) and host1[n]
+ * (values, keyed only) are copied to the device at admission, as
+ * scl_server_submit_load does.  host0 == NULL: the task runs on its resident
+ * partition tasks[i].part. */
+typedef struct {
+    const void* host0;
+    const void* host1;
+    uint64_t n;
+    int32_t dtype;       /* scl_dtype */
+    uint32_t reserved;
+} scl_task_data;
+
+/* scl_server_replay where some tasks bring new data (data[i].host0 != NULL):
+ * their host-to-device copy is part of their latency.  Results are collected
+ * while the trace is still being submitted. */
+int scl_server_replay_load(scl_ctx* ctx, const scl_task* tasks, const scl_task_data* data,
+                           const double* arrival_s, uint32_t n, int64_t* latency_ns,
+                           scl_result* results);
 
 /* ------------------------------------------------------ device-polling server */
 

@@ -217,6 +217,16 @@ int scl_load_partition_kv(scl_ctx* ctx, const int32_t* keys, const float* vals, 
     return SCL_OK;
 }
 
+int scl_alloc_partition(scl_ctx* ctx, scl_dtype dtype, uint64_t n, scl_part* out) {
+    CTX_ENTER(ctx);
+    if (!out) return fail(SCL_E_INVALID, "null output");
+    if ((int)dtype < 0 || dtype > SCL_KV_I32_F32) return fail(SCL_E_INVALID, "bad dtype");
+    Partition p;
+    SCL_TRY(new_partition(ctx, dtype, n, &p));
+    *out = register_partition(ctx, p);
+    return SCL_OK;
+}
+
 int scl_wrap_device(scl_ctx* ctx, void* dev0, void* dev1, scl_dtype dtype, uint64_t n,
                     scl_part* out) {
     CTX_ENTER(ctx);

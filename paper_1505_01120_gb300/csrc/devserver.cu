@@ -570,6 +570,23 @@ int scl_devserver_replay(scl_ctx* ctx, const scl_task* tasks, const double* arri
     std::vector<uint64_t> tickets(n, 0);
     std::vector<int64_t> sched(n);
     std::vector<int> sub_status(n, SCL_OK);
+    std::vector<int> wait_status(n, SCL_OK);
+    // A collector thread takes each result as soon as it is done, so the map
+    // of finished results stays small however long the trace is.
+    std::atomic<uint32_t> published{0};
+    std::thread collector([&] {
+        for (uint32_t i = 0; i < n; ++i) {
+            while (published.load(std::memory_order_acquire) <= i) std::this_thread::yield();
+            if (sub_status[i] != SCL_OK) continue;
+            Done d;
+            if (!s->wait_done(tickets[i], 0, 60000000000ll, &d)) {
+                wait_status[i] = SCL_E_TIMEOUT;
+                continue;
+            }
+            if (latency_ns) latency_ns[i] = d.t_done - sched[i];
+            if (results) results[i] = d.r;
+        }
+    });
     const int64_t t0 = now_ns() + 1000000;   // start 1 ms from now
     for (uint32_t i = 0; i < n; ++i) {
         sched[i] = t0 + (int64_t)(arrival_s[i] * 1e9);
@@ -581,20 +598,15 @@ int scl_devserver_replay(scl_ctx* ctx, const scl_task* tasks, const double* arri
         }
         // open loop: latency counts from the scheduled arrival
         sub_status[i] = dsrv_submit(ctx, s, tasks[i], sched[i], &tickets[i]);
+        published.store(i + 1, std::memory_order_release);
     }
+    collector.join();
     int worst = SCL_OK;
     for (uint32_t i = 0; i < n; ++i) {
-        int st = sub_status[i];
-        if (st == SCL_OK) {
-            Done d;
-            if (!s->wait_done(tickets[i], 0, 60000000000ll, &d)) {
-                st = fail(SCL_E_TIMEOUT, "task %u not done after 60 s", i);
-            } else {
-                if (latency_ns) latency_ns[i] = d.t_done - sched[i];
-                if (results) results[i] = d.r;
-                continue;
-            }
-        }
+        int st = sub_status[i] != SCL_OK ? sub_status[i] : wait_status[i];
+        if (st == SCL_OK) continue;
+        if (st == SCL_E_TIMEOUT && sub_status[i] == SCL_OK)
+            st = fail(SCL_E_TIMEOUT, "task %u not done after 60 s", i);
         if (latency_ns) latency_ns[i] = -1;
         if (results) {
             memset(&results[i], 0, sizeof results[i]);

@@ -46,6 +46,27 @@ __host__ __device__ constexpr uint32_t kKeyedHeadWords(uint32_t block) {
 }
 // Shared memory of a keyed CTA (blocks of up to 512 threads): table, copies.
 constexpr uint32_t kKeyedSmemBytes = (kKeyedTableWords + kKeyedHeadWords(512)) * 4;
+// Fixed-point windows of the keyed-only kernel (Sec. 3.2.3's reduce-by-key
+// with integer table adds).  Shared-memory integer adds cost about half of
+// fp32 adds under random-key bank conflicts on GB300, so a piece's values in
+// [B * 2^-kFixTinyBits, B) -- B the power of two just above the largest value
+// of its first chunk -- are added as int32 multiples of 2^-F, F chosen so that
+// fewer than 2^kFixCountBits such adds to one key cannot overflow.  The int32
+// sums are folded into the fp32 table every kFixWindow pairs; a window in
+// which a key took 2^kFixCountBits pairs or more makes the piece run again on
+// the fp32 table alone.  Each value's rounding error is below
+// 2^(kFixCountBits + kFixTinyBits - 32) = 2^-18 of its magnitude.  Values
+// whose magnitude is outside the window (smaller, larger, non-finite) take
+// fp32 adds; the sign does not matter; zeros add nothing.
+constexpr uint32_t kFixCountBits = 9;
+constexpr uint32_t kFixTinyBits = 5;
+constexpr uint64_t kFixWindow = 65536;        // pairs per window, a multiple of every chunk
+constexpr uint64_t kFixMinPairs = 16384;      // shorter pieces use the fp32 table only
+constexpr uint32_t kFixMinKeys = 1024;        // smaller key spaces use the fp32 table only
+constexpr uint32_t kFixSumOffset = kKeyedSmemBytes;              // int32 window sums
+constexpr uint32_t kFixSnapOffset = kFixSumOffset + kMaxKeys * 4; // counts at the window's start
+constexpr uint32_t kFixMaxOffset = kFixSnapOffset + kMaxKeys * 4; // per-warp maxima
+constexpr uint32_t kKeyedFastSmemBytes = kFixMaxOffset + 16 * 4;
 constexpr uint64_t kKeyedPieceAlign = 64;           // piece boundaries, in pairs
 constexpr uint64_t kKeyedMinPiece = 32768;          // pairs; keeps table flushes cheap
 constexpr uint64_t kKeyedMinFragment = 8192;        // pairs; shorter end pieces join a neighbour
@@ -103,7 +124,7 @@ struct KPiece {             // one keyed piece: pairs [begin, end) of a task
 static_assert(sizeof(KPiece) == 24, "KPiece layout");
 
 struct alignas(16) StreamPartial {  // one streaming segment's partial
-    double s;       // fp64 sum (fp32 kinds)
+    float shi, slo; // sum (fp32 kinds) as a float-float pair: shi + slo
     uint64_t u;     // uint64 sum (uint32 kinds)
     float mn, mx;
     uint32_t pad[2];

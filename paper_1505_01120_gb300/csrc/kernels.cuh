@@ -80,10 +80,60 @@ __device__ __forceinline__ float map_f32(float x, float a, float b, float c) {
     else return x;
 }
 
+// --------------------------------------------------- float-float sums
+
+// Sums past one thread's chunk are carried as float-float pairs (hi + lo, two
+// fp32 words, about 44 bits of precision) on the fp32 pipe: GB300 runs fp64
+// adds at a small fraction of its fp32 rate, and fp64 block trees saturated
+// its fp64 pipe on batches of small partitions.  two_sum is exact (hi + lo
+// equals a + b) and its result does not depend on the operand order, so a
+// xor-butterfly leaves the same pair in every lane.  A non-finite hi keeps lo
+// at zero, so inf and NaN propagate as in fp64.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+    return ff{s, isfinite(s) ? e : 0.f};
+}
+
+// a + b with |a| >= |b| (or a zero).
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return ff{s, isfinite(s) ? e : 0.f};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const ff s = ff_two_sum(x.hi, y.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ ff ff_add_f(ff x, float y) {
+    const ff s = ff_two_sum(x.hi, y);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+
+// The pair of a double: hi its fp32 rounding, lo the rounding of the rest.
+__device__ __forceinline__ ff ff_of_double(double d) {
+    const float hi = (float)d;
+    return ff{hi, isfinite(hi) ? (float)(d - (double)hi) : 0.f};
+}
+
+__device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ ff ff_shfl_xor(ff x, int o) {
+    return ff{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
 // ------------------------------------------------------ block reductions
 
 struct RedSmem {
-    double d[32];
+    float shi[32], slo[32];
     unsigned long long u[32];
     float mn[32];
     float mx[32];
@@ -109,27 +159,28 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 }
 
 template <int BLOCK>
-__device__ __forceinline__ void block_reduce_f(double& s, float& mn, float& mx, RedSmem& sm) {
+__device__ __forceinline__ void block_reduce_ff(ff& s, float& mn, float& mx, RedSmem& sm) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s = ff_add(s, ff_shfl_xor(s, o));
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
-        sm.d[w] = s;
+        sm.shi[w] = s.hi;
+        sm.slo[w] = s.lo;
         sm.mn[w] = mn;
         sm.mx[w] = mx;
     }
     __syncthreads();
     const bool in = l < BLOCK / 32;
-    s = in ? sm.d[l] : 0.0;
+    s = in ? ff{sm.shi[l], sm.slo[l]} : ff{0.f, 0.f};
     mn = in ? sm.mn[l] : CUDART_INF_F;
     mx = in ? sm.mx[l] : -CUDART_INF_F;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s = ff_add(s, ff_shfl_xor(s, o));
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
@@ -171,7 +222,7 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
     const float ca = t.coef[0], cb = t.coef[1], cc = t.coef[2];
 
     unsigned long long usum = 0;
-    double dsum = 0.0;
+    ff fsum{0.f, 0.f};
     float mn = CUDART_INF_F, mx = -CUDART_INF_F;
 
     uint64_t i = b;
@@ -193,7 +244,7 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
                     mn = fminf(mn, fminf(fminf(y0, y1), fminf(y2, y3)));
                     mx = fmaxf(mx, fmaxf(fmaxf(y0, y1), fmaxf(y2, y3)));
                 }
-                dsum += (double)cs;
+                fsum = ff_add_f(fsum, cs);
             } else {
 #pragma unroll
                 for (int j = 0; j < IPT; ++j) {
@@ -237,21 +288,22 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
                     if (ok[q]) usum += (unsigned long long)map_u32<KIND>(w[q]);
             }
         }
-        if constexpr (F32) dsum += (double)cs;
+        if constexpr (F32) fsum = ff_add_f(fsum, cs);
     }
 
-    if constexpr (F32) block_reduce_f<BLOCK>(dsum, mn, mx, sm);
+    if constexpr (F32) block_reduce_ff<BLOCK>(fsum, mn, mx, sm);
     else usum = block_sum_u64<BLOCK>(usum, sm);
-    if constexpr (!F32) dsum = (double)usum;
 
     if (t.nseg == 1) {
         if (threadIdx.x == 0)
-            write_result(t.result, usum, dsum, F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, t.n, t.kind);
+            write_result(t.result, usum, F32 ? ff_to_double(fsum) : (double)usum,
+                         F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, t.n, t.kind);
         return threadIdx.x == 0;
     }
     if (threadIdx.x == 0) {
         StreamPartial* sp = a.spart + t.slot0 + local;
-        sp->s = dsum;
+        sp->shi = fsum.hi;
+        sp->slo = fsum.lo;
         sp->u = usum;
         sp->mn = mn;
         sp->mx = mx;
@@ -264,26 +316,24 @@ __device__ __forceinline__ bool stream_segment(const KernelArgs& a, const DevTas
     __threadfence();
 
     // This CTA finished the task's last segment: fold the partials in slot order.
-    double fs = 0.0;
+    ff fs{0.f, 0.f};
     unsigned long long fu = 0;
     float fmn = CUDART_INF_F, fmx = -CUDART_INF_F;
     for (uint32_t s = threadIdx.x; s < t.nseg; s += BLOCK) {
         const StreamPartial* sp = a.spart + t.slot0 + s;
         if constexpr (F32) {
-            fs += __ldcg(&sp->s);
+            fs = ff_add(fs, ff{__ldcg(&sp->shi), __ldcg(&sp->slo)});
             fmn = fminf(fmn, __ldcg(&sp->mn));
             fmx = fmaxf(fmx, __ldcg(&sp->mx));
         } else {
             fu += __ldcg(reinterpret_cast<const unsigned long long*>(&sp->u));
         }
     }
-    if constexpr (F32) block_reduce_f<BLOCK>(fs, fmn, fmx, sm);
-    else {
-        fu = block_sum_u64<BLOCK>(fu, sm);
-        fs = (double)fu;
-    }
+    if constexpr (F32) block_reduce_ff<BLOCK>(fs, fmn, fmx, sm);
+    else fu = block_sum_u64<BLOCK>(fu, sm);
     if (threadIdx.x == 0) {
-        write_result(t.result, fu, fs, F32 ? fmn : 0.f, F32 ? fmx : 0.f, SCL_OK, t.n, t.kind);
+        write_result(t.result, fu, F32 ? ff_to_double(fs) : (double)fu, F32 ? fmn : 0.f,
+                     F32 ? fmx : 0.f, SCL_OK, t.n, t.kind);
         a.tickets[task] = 0u;   // ready for the next launch
     }
     return threadIdx.x == 0;
@@ -323,35 +373,92 @@ __device__ __forceinline__ void keyed_add(uint32_t k, uint32_t v, uint32_t nk, u
     }
 }
 
-// Pairs [b, e) of a keyed task accumulated into the CTA's shared-memory table
-// (count[kMaxKeys] then fp32 sum[kMaxKeys], then the head copies), zeroed
-// first; the head copies are folded into the table at the end.  Returns, in
-// every thread, whether any key was out of range.  Ends with a barrier.
-template <int BLOCK, int IPT, bool HASHED>
-__device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, uint64_t e,
-                                                uint32_t* tab) {
+// The fixed-point window of one piece: magnitudes with bit patterns in
+// [lo, lo + span) are added to the int32 sums as round(v * scale), scale =
+// 2^F; inv = 2^-F folds them back.
+struct FixWin {
+    float scale, inv;
+    uint32_t lo, span;
+};
+
+// As keyed_add, with values inside the window added to the int32 sums.
+template <bool HASHED>
+__device__ __forceinline__ void keyed_add_fix(uint32_t k, uint32_t v, uint32_t nk, uint32_t* cnt,
+                                              float* sum, float* head, int32_t* isum,
+                                              const FixWin& w, uint32_t& bad) {
+    if constexpr (HASHED) k = __umulhi(mix32(k), nk);
+    if (k < nk) {
+        atomicAdd(&cnt[k], 1u);
+        const uint32_t ab = v & 0x7fffffffu;
+        if (!HASHED && k < kKeyedHead)
+            atomicAdd(&head[k], __uint_as_float(v));
+        else if (ab - w.lo < w.span)
+            atomicAdd(&isum[k], __float2int_rn(__uint_as_float(v) * w.scale));
+        else if (ab != 0u)   // a zero of either sign adds nothing
+            atomicAdd(&sum[k], __uint_as_float(v));
+    } else {
+        bad = 1u;
+    }
+}
+
+// Folds the window's int32 sums into the fp32 table and starts a new window;
+// returns nonzero in a thread if one of its keys took 2^kFixCountBits pairs
+// or more in the window (its int32 sum may have wrapped).  Call between
+// barriers.
+template <int BLOCK, bool HASHED>
+__device__ __forceinline__ uint32_t fix_fold(uint32_t nk, const uint32_t* cnt, float* sum,
+                                             int32_t* isum, uint32_t* snap, float inv) {
+    uint32_t over = 0;
+    for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+        const uint32_t c = cnt[k];
+        if (HASHED || k >= kKeyedHead) over |= (uint32_t)(c - snap[k] >= (1u << kFixCountBits));
+        const int32_t q = isum[k];
+        if (q != 0) {
+            sum[k] += (float)q * inv;
+            isum[k] = 0;
+        }
+        snap[k] = c;
+    }
+    return over;
+}
+
+// One pass over pairs [b, e): 128-bit loads of IPT vectors of keys and of
+// values per thread, then the table adds.  FIX: through the fixed-point
+// window, folded every kFixWindow pairs and at the end; returns nonzero in
+// every thread if a window overflowed.
+template <int BLOCK, int IPT, bool HASHED, bool FIX>
+__device__ __forceinline__ uint32_t keyed_pass(const DevTask& t, uint64_t b, uint64_t e,
+                                               uint32_t* tab, float* head, const FixWin& w,
+                                               uint32_t& bad) {
     constexpr uint32_t CH = BLOCK * IPT * 4;
-    static_assert(kKeyedHeadWords(BLOCK) * 4 + kKeyedTableWords * 4 <= kKeyedSmemBytes, "smem");
+    static_assert(kFixWindow % CH == 0, "windows hold whole chunks");
     uint32_t* cnt = tab;
     float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
-    float* heads = reinterpret_cast<float*>(tab + kKeyedTableWords);
-    float* head = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
-                           (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
+    int32_t* isum = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(tab) + kFixSumOffset);
+    uint32_t* snap = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixSnapOffset);
     const uint32_t nk = t.num_keys;
-    for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
-        cnt[k] = 0u;
-        sum[k] = 0.f;
-    }
-    if (!HASHED)
-        for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(BLOCK); i += BLOCK) heads[i] = 0.f;
-    __syncthreads();
-
     const char* kb = static_cast<const char*>(t.in0);
     const char* vb = static_cast<const char*>(t.in1);
-    uint32_t bad = 0;
+    uint32_t over = 0;
+    uint64_t next_fold = b + kFixWindow;
+    auto add = [&](uint32_t k, uint32_t v) {
+        if constexpr (FIX) keyed_add_fix<HASHED>(k, v, nk, cnt, sum, head, isum, w, bad);
+        else keyed_add<HASHED>(k, v, nk, cnt, sum, head, bad);
+    };
+    auto window = [&](uint64_t i) {   // CTA-uniform
+        if constexpr (FIX) {
+            if (i >= next_fold) {
+                __syncthreads();
+                over |= fix_fold<BLOCK, HASHED>(nk, cnt, sum, isum, snap, w.inv);
+                __syncthreads();
+                next_fold += kFixWindow;
+            }
+        }
+    };
     uint64_t i = b;
     if (t.flags & TF_ALIGNED) {
         for (; i + CH <= e; i += CH) {
+            window(i);
             uint4 kv[IPT], vv[IPT];
             const uint64_t off = (i + (uint64_t)threadIdx.x * 4) * 4;
 #pragma unroll
@@ -360,23 +467,131 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
             for (int j = 0; j < IPT; ++j) vv[j] = ld_stream_v4(vb + off + (size_t)j * BLOCK * 16);
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
-                keyed_add<HASHED>(kv[j].x, vv[j].x, nk, cnt, sum, head, bad);
-                keyed_add<HASHED>(kv[j].y, vv[j].y, nk, cnt, sum, head, bad);
-                keyed_add<HASHED>(kv[j].z, vv[j].z, nk, cnt, sum, head, bad);
-                keyed_add<HASHED>(kv[j].w, vv[j].w, nk, cnt, sum, head, bad);
+                add(kv[j].x, vv[j].x);
+                add(kv[j].y, vv[j].y);
+                add(kv[j].z, vv[j].z);
+                add(kv[j].w, vv[j].w);
             }
         }
     }
     for (; i < e; i += CH) {
+        window(i);
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint64_t g = i + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (g + q < e)
-                    keyed_add<HASHED>(ld_stream_b32(kb + (g + q) * 4),
-                                      ld_stream_b32(vb + (g + q) * 4), nk, cnt, sum, head, bad);
+                if (g + q < e) add(ld_stream_b32(kb + (g + q) * 4), ld_stream_b32(vb + (g + q) * 4));
         }
+    }
+    if constexpr (FIX) {
+        __syncthreads();
+        over |= fix_fold<BLOCK, HASHED>(nk, cnt, sum, isum, snap, w.inv);
+        return (uint32_t)__syncthreads_or((int)over);
+    }
+    return 0u;
+}
+
+// Zeroes the count and fp32 sum of ids [0, nk) and the head copies (and, with
+// FIX, the int32 sums and count snapshots).  Call between barriers.
+template <int BLOCK, bool HASHED, bool FIX>
+__device__ __forceinline__ void keyed_zero(uint32_t* tab, uint32_t nk) {
+    uint32_t* cnt = tab;
+    float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
+    float* heads = reinterpret_cast<float*>(tab + kKeyedTableWords);
+    for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+        cnt[k] = 0u;
+        sum[k] = 0.f;
+        if constexpr (FIX) {
+            reinterpret_cast<int32_t*>(reinterpret_cast<char*>(tab) + kFixSumOffset)[k] = 0;
+            reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixSnapOffset)[k] = 0u;
+        }
+    }
+    if (!HASHED)
+        for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(BLOCK); i += BLOCK) heads[i] = 0.f;
+}
+
+// Largest finite |v| (as a bit pattern) over this thread's pairs of the first
+// chunk of [b, e); the chunk's values are read again from L2 by the pass.
+template <int BLOCK, int IPT>
+__device__ __forceinline__ uint32_t first_chunk_max(const DevTask& t, uint64_t b, uint64_t e) {
+    const char* vb = static_cast<const char*>(t.in1);
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const uint64_t g = b + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (g + q < e) {
+                const uint32_t ab = ld_stream_b32(vb + (g + q) * 4) & 0x7fffffffu;
+                if (ab < 0x7f800000u) m = max(m, ab);
+            }
+    }
+    return m;
+}
+
+// The window of a piece whose first chunk's largest finite magnitude has the
+// bit pattern m: B = 2^(E+1) for m in [2^E, 2^(E+1)), F = 31 - kFixCountBits
+// - (E+1), so |round(v * 2^F)| <= 2^(31 - kFixCountBits) for |v| < B.  False
+// if m is zero or outside [2^-90, 2^90) (the pass then uses fp32 adds only).
+__device__ __forceinline__ bool fix_window(uint32_t m, FixWin* w) {
+    if (m < 0x12800000u || m >= 0x6c800000u) return false;   // [2^-90, 2^90)
+    const int e1 = (int)(m >> 23) - 127 + 1;                    // B = 2^e1
+    const int F = 31 - (int)kFixCountBits - e1;
+    w->scale = __uint_as_float((uint32_t)(F + 127) << 23);
+    w->inv = __uint_as_float((uint32_t)(127 - F) << 23);
+    w->lo = (uint32_t)(e1 - (int)kFixTinyBits + 127) << 23;
+    w->span = ((uint32_t)(e1 + 127) << 23) - w->lo;
+    return true;
+}
+
+// Pairs [b, e) of a keyed task accumulated into the CTA's shared-memory table
+// (count[kMaxKeys] then fp32 sum[kMaxKeys], then the head copies), zeroed
+// first; the head copies are folded into the table at the end.  FAST (the
+// keyed-only kernel, whose CTAs have kKeyedFastSmemBytes of shared memory):
+// long pieces over large key spaces go through the fixed-point window, and a
+// piece whose window overflowed runs again on the fp32 table alone.  Returns,
+// in every thread, whether any key was out of range.  Ends with a barrier.
+template <int BLOCK, int IPT, bool HASHED, bool FAST = false>
+__device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, uint64_t e,
+                                                uint32_t* tab) {
+    static_assert(kKeyedHeadWords(BLOCK) * 4 + kKeyedTableWords * 4 <= kKeyedSmemBytes, "smem");
+    static_assert(BLOCK / 32 <= 16, "per-warp maxima");
+    float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
+    float* heads = reinterpret_cast<float*>(tab + kKeyedTableWords);
+    float* head = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
+                           (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
+    const uint32_t nk = t.num_keys;
+    FixWin w{0.f, 0.f, 0u, 0u};
+    uint32_t bad = 0;
+    bool done = false;
+    if constexpr (FAST) {
+        if (nk >= kFixMinKeys && e - b >= kFixMinPairs) {
+            uint32_t* wmax =
+                reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixMaxOffset);
+            const uint32_t m = __reduce_max_sync(0xffffffffu, first_chunk_max<BLOCK, IPT>(t, b, e));
+            if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+            keyed_zero<BLOCK, HASHED, true>(tab, nk);
+            __syncthreads();
+            uint32_t mm = 0;
+#pragma unroll
+            for (int q = 0; q < BLOCK / 32; ++q) mm = max(mm, wmax[q]);
+            if (!fix_window(mm, &w)) {
+                keyed_pass<BLOCK, IPT, HASHED, false>(t, b, e, tab, head, w, bad);
+            } else if (keyed_pass<BLOCK, IPT, HASHED, true>(t, b, e, tab, head, w, bad)) {
+                // a window overflowed: run the piece again on the fp32 table
+                keyed_zero<BLOCK, HASHED, false>(tab, nk);
+                __syncthreads();
+                bad = 0;
+                keyed_pass<BLOCK, IPT, HASHED, false>(t, b, e, tab, head, w, bad);
+            }
+            done = true;
+        }
+    }
+    if (!done) {
+        keyed_zero<BLOCK, HASHED, false>(tab, nk);
+        __syncthreads();
+        keyed_pass<BLOCK, IPT, HASHED, false>(t, b, e, tab, head, w, bad);
     }
     const int any_bad = __syncthreads_or((int)bad);
     if (!HASHED) {
@@ -390,18 +605,18 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
 // shared-memory table (count, fp32 sum) and written to the outputs (single
 // piece) or to partial slot slot0 + slot.  Returns true in thread 0 if it
 // wrote the task's result (single piece).
-template <int BLOCK, int IPT, bool HASHED>
+template <int BLOCK, int IPT, bool HASHED, bool FAST>
 __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
                                             uint32_t slot, uint64_t b, uint64_t e,
                                             uint32_t* tab, RedSmem& sm) {
-    const int any_bad = keyed_accumulate<BLOCK, IPT, HASHED>(t, b, e, tab);
+    const int any_bad = keyed_accumulate<BLOCK, IPT, HASHED, FAST>(t, b, e, tab);
     const uint32_t* cnt = tab;
     const float* sum = reinterpret_cast<const float*>(tab + kMaxKeys);
     const uint32_t nk = t.num_keys;
     bool wrote = false;
     if (t.nseg == 1) {
         unsigned long long ctot = 0;
-        double stot = 0.0;
+        ff stot{0.f, 0.f};
         for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
             const uint32_t c = cnt[k];
             const float s = sum[k];
@@ -409,13 +624,13 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
             t.sums_out[k] = s;
             if (t.sums64_out) t.sums64_out[k] = (double)s;
             ctot += c;
-            stot += (double)s;
+            stot = ff_add_f(stot, s);
         }
         float dummy0 = CUDART_INF_F, dummy1 = -CUDART_INF_F;
-        block_reduce_f<BLOCK>(stot, dummy0, dummy1, sm);
+        block_reduce_ff<BLOCK>(stot, dummy0, dummy1, sm);
         ctot = block_sum_u64<BLOCK>(ctot, sm);
         if (threadIdx.x == 0) {
-            write_result(t.result, ctot, stot, CUDART_INF_F, -CUDART_INF_F,
+            write_result(t.result, ctot, ff_to_double(stot), CUDART_INF_F, -CUDART_INF_F,
                          any_bad ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
             wrote = true;
         }
@@ -435,13 +650,16 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
 
 // Residency targets, as register caps: the streaming-only kernels get a full
 // SM of threads (32 registers; the uint32 kernel's 64-bit accumulators would
-// otherwise take 40 and cost two CTAs per SM of loads in flight), kernels
-// with a keyed table half of it (64 registers; the table allows 6 CTAs, and
-// without a target ptxas takes up to 168 registers for the mixed kernel).
+// otherwise take 40 and cost two CTAs per SM of loads in flight), the mixed
+// kernel half of it (64 registers; its table allows 5 CTAs, and without a
+// target ptxas takes up to 168 registers), the keyed-only kernel three
+// 256-thread CTAs (its fixed-point window's shared memory allows no more).
 // At 2 items per thread the 32-register cap would spill; those shapes get 42.
 template <int MASK, int BLOCK, int IPT>
 constexpr int persistent_min_blocks() {
-    return (MASK == M_U32 || MASK == M_F32) ? (IPT >= 4 ? 2048 : 1536) / BLOCK : 1024 / BLOCK;
+    return (MASK == M_U32 || MASK == M_F32) ? (IPT >= 4 ? 2048 : 1536) / BLOCK
+           : MASK == M_KEYED                ? (BLOCK == 256 ? 3 : 2)
+                                            : 1024 / BLOCK;
 }
 
 template <int BLOCK, int IPT, int MASK>
@@ -456,6 +674,8 @@ __global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT
         // loads and cap the kernel at 2 CTAs per SM.  Keyed results do not
         // depend on the shape (exact counts; sums from shared-memory atomics).
         constexpr int KIPT = (MASK == M_ALL && IPT > 4) ? 4 : IPT;
+        // The keyed-only kernel has the shared memory of the fixed-point window.
+        constexpr bool FAST = MASK == M_KEYED;
         uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
         if (a.tasks == nullptr) {
             if (is_keyed(a.single.kind) && blockIdx.x < a.nkeyed_ctas) {
@@ -463,9 +683,9 @@ __global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT
                 const uint64_t b = keyed_single_bound(a.single.n, blockIdx.x, G);
                 const uint64_t e = keyed_single_bound(a.single.n, blockIdx.x + 1, G);
                 if (a.single.kind == K_KEYED_MIX)
-                    keyed_piece<BLOCK, KIPT, true>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
+                    keyed_piece<BLOCK, KIPT, true, FAST>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
                 else
-                    keyed_piece<BLOCK, KIPT, false>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
+                    keyed_piece<BLOCK, KIPT, false, FAST>(a, a.single, 0u, blockIdx.x, b, e, tab, sm);
             }
         } else {
             const uint32_t p0 = a.kp_first[blockIdx.x], p1 = a.kp_first[blockIdx.x + 1];
@@ -473,9 +693,9 @@ __global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT
                 const KPiece kp = a.kpieces[p];
                 const DevTask t = a.tasks[kp.task];
                 if (t.kind == K_KEYED_MIX)
-                    keyed_piece<BLOCK, KIPT, true>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, true, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
                 else
-                    keyed_piece<BLOCK, KIPT, false>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, false, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
             }
         }
     }
@@ -549,12 +769,12 @@ __global__ void __launch_bounds__(FB) k_keyed_fold(const __grid_constant__ Kerne
 
     const uint32_t k = blockIdx.x * kFoldBlock + threadIdx.x;
     unsigned long long ctot = 0;
-    double stot = 0.0;
+    ff stot{0.f, 0.f};
     if (k < nk) {
         const uint32_t* src = a.kpart + (size_t)t.slot0 * kKeyedTableWords + k;
         const uint32_t np = t.nseg;
         uint32_t c = 0;
-        double s = 0.0;
+        ff s{0.f, 0.f};
         uint32_t p = 0;
         for (; p + 4 <= np; p += 4) {
             uint32_t cc[4], sv[4];
@@ -566,39 +786,41 @@ __global__ void __launch_bounds__(FB) k_keyed_fold(const __grid_constant__ Kerne
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 c += cc[q];
-                s += (double)__uint_as_float(sv[q]);
+                s = ff_add_f(s, __uint_as_float(sv[q]));
             }
         }
         for (; p < np; ++p) {
             c += __ldcg(src + (size_t)p * kKeyedTableWords);
-            s += (double)__uint_as_float(__ldcg(src + (size_t)p * kKeyedTableWords + kMaxKeys));
+            s = ff_add_f(s, __uint_as_float(__ldcg(src + (size_t)p * kKeyedTableWords + kMaxKeys)));
         }
+        const double sd = ff_to_double(s);
         t.counts_out[k] = c;
-        t.sums_out[k] = (float)s;
-        if (t.sums64_out) t.sums64_out[k] = s;
+        t.sums_out[k] = (float)sd;
+        if (t.sums64_out) t.sums64_out[k] = sd;
         ctot = c;
         stot = s;
     }
     float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
-    block_reduce_f<kFoldBlock>(stot, d0, d1, sm);
+    block_reduce_ff<kFoldBlock>(stot, d0, d1, sm);
     ctot = block_sum_u64<kFoldBlock>(ctot, sm);
     if (threadIdx.x == 0) {
         StreamPartial* fp = a.fpart + (size_t)fi * (kMaxKeys / kFoldBlock) + blockIdx.x;
-        fp->s = stot;
+        fp->shi = stot.hi;
+        fp->slo = stot.lo;
         fp->u = ctot;
         __threadfence();
         const uint32_t prev = atomicAdd(&a.tickets[task], 1u);
         if (prev == nkb - 1) {
             __threadfence();
-            double s = 0.0;
+            ff s{0.f, 0.f};
             unsigned long long c = 0;
             for (uint32_t kb = 0; kb < nkb; ++kb) {
                 const StreamPartial* q = a.fpart + (size_t)fi * (kMaxKeys / kFoldBlock) + kb;
-                s += __ldcg(&q->s);
+                s = ff_add(s, ff{__ldcg(&q->shi), __ldcg(&q->slo)});
                 c += __ldcg(reinterpret_cast<const unsigned long long*>(&q->u));
             }
             const uint32_t fl = atomicExch(&a.task_flags[task], 0u);
-            write_result(t.result, c, s, CUDART_INF_F, -CUDART_INF_F,
+            write_result(t.result, c, ff_to_double(s), CUDART_INF_F, -CUDART_INF_F,
                          fl ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
             a.tickets[task] = 0u;
         }
@@ -816,20 +1038,20 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
     static_assert(FB == 256, "finish block");
     __shared__ RedSmem sm;
     unsigned long long c = 0;
-    double s = 0.0;
+    ff s{0.f, 0.f};
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.num_keys;
          k += (uint64_t)gridDim.x * blockDim.x) {
         const double v = a.sums64[k];
         a.sums32[k] = (float)v;
         c += a.counts[k];
-        s += v;
+        s = ff_add(s, ff_of_double(v));
     }
     float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
-    block_reduce_f<256>(s, d0, d1, sm);
+    block_reduce_ff<256>(s, d0, d1, sm);
     c = block_sum_u64<256>(c, sm);
     if (threadIdx.x == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.result->u64_sum), c);
-        atomicAdd(&a.result->f64_sum, s);
+        atomicAdd(&a.result->f64_sum, ff_to_double(s));
         __threadfence();
         if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
             __threadfence();
@@ -856,7 +1078,10 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
 
 // Instantiate the persistent kernel for one mask over the tuned shapes and
 // define kernel_table_<name>().
-#define SCL_DYN(M) (scl::mask_has_keyed(M) ? scl::kKeyedSmemBytes : 0)
+#define SCL_DYN(M)                                             \
+    ((M) == scl::M_KEYED          ? scl::kKeyedFastSmemBytes     \
+     : scl::mask_has_keyed(M)     ? scl::kKeyedSmemBytes         \
+                                  : 0)
 #define SCL_SHAPE(M, B, I) {M, B, I, (const void*)&scl::dev::k_persistent<B, I, M>, SCL_DYN(M), 0, 0}
 #define SCL_DEFINE_TABLE(NAME, M)                                                   \
     namespace scl {                                                                 \

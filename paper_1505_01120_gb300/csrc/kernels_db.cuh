@@ -233,8 +233,8 @@ __device__ __forceinline__ bool db_keyed_unit(const DbArgs& a, const DevTask& t,
     constexpr int IPT = IPT_STREAM > 4 ? 4 : IPT_STREAM;
     if (t.nseg == 1) {
         if (t.kind == K_KEYED_MIX)
-            return keyed_piece<BLOCK, IPT, true>(a.ka, t, j, 0u, 0ull, t.n, tab, sm);
-        return keyed_piece<BLOCK, IPT, false>(a.ka, t, j, 0u, 0ull, t.n, tab, sm);
+            return keyed_piece<BLOCK, IPT, true, false>(a.ka, t, j, 0u, 0ull, t.n, tab, sm);
+        return keyed_piece<BLOCK, IPT, false, false>(a.ka, t, j, 0u, 0ull, t.n, tab, sm);
     }
     const uint64_t b = keyed_single_bound(t.n, local, t.nseg);
     const uint64_t e = keyed_single_bound(t.n, local + 1, t.nseg);
@@ -266,7 +266,7 @@ __device__ __forceinline__ bool db_keyed_unit(const DbArgs& a, const DevTask& t,
 
     // Last piece: the outputs, then the accumulator back to zero.
     unsigned long long ctot = 0;
-    double stot = 0.0;
+    ff stot{0.f, 0.f};
     for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
         const uint32_t c = __ldcg(&acnt[k]);
         const double s = __ldcg(&asum[k]);
@@ -276,14 +276,14 @@ __device__ __forceinline__ bool db_keyed_unit(const DbArgs& a, const DevTask& t,
         acnt[k] = 0u;
         asum[k] = 0.0;
         ctot += c;
-        stot += s;
+        stot = ff_add(stot, ff_of_double(s));
     }
     float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
-    block_reduce_f<BLOCK>(stot, d0, d1, sm);
+    block_reduce_ff<BLOCK>(stot, d0, d1, sm);
     ctot = block_sum_u64<BLOCK>(ctot, sm);
     if (threadIdx.x == 0) {
         const uint32_t fl = atomicExch(&a.ka.task_flags[j], 0u);
-        write_result(t.result, ctot, stot, CUDART_INF_F, -CUDART_INF_F,
+        write_result(t.result, ctot, ff_to_double(stot), CUDART_INF_F, -CUDART_INF_F,
                      fl ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
         a.ka.tickets[j] = 0u;
     }

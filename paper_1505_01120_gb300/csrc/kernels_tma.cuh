@@ -99,7 +99,7 @@ __device__ __forceinline__ void named_sync() {
 }
 
 // Block reductions over the CB consumer threads (tid = consumer index), the
-// same butterfly-then-warp-totals order as block_sum_u64 / block_reduce_f.
+// same butterfly-then-warp-totals order as block_sum_u64 / block_reduce_ff.
 template <int CB>
 __device__ __forceinline__ unsigned long long csum_u64(unsigned long long v, uint32_t tid,
                                                        RedSmem& sm) {
@@ -116,28 +116,29 @@ __device__ __forceinline__ unsigned long long csum_u64(unsigned long long v, uin
 }
 
 template <int CB>
-__device__ __forceinline__ void creduce_f(double& s, float& mn, float& mx, uint32_t tid,
-                                          RedSmem& sm) {
+__device__ __forceinline__ void creduce_ff(ff& s, float& mn, float& mx, uint32_t tid,
+                                           RedSmem& sm) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s = ff_add(s, ff_shfl_xor(s, o));
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     const int w = tid >> 5, l = tid & 31;
     if (l == 0) {
-        sm.d[w] = s;
+        sm.shi[w] = s.hi;
+        sm.slo[w] = s.lo;
         sm.mn[w] = mn;
         sm.mx[w] = mx;
     }
     named_sync<CB>();
     const bool in = l < CB / 32;
-    s = in ? sm.d[l] : 0.0;
+    s = in ? ff{sm.shi[l], sm.slo[l]} : ff{0.f, 0.f};
     mn = in ? sm.mn[l] : CUDART_INF_F;
     mx = in ? sm.mx[l] : -CUDART_INF_F;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s = ff_add(s, ff_shfl_xor(s, o));
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
@@ -159,7 +160,7 @@ struct TmaLayout {
 template <int CB, int IPT, int KIND>
 __device__ __forceinline__ void consume_chunk(const StageMeta& m, const char* stage,
                                               uint32_t tid, unsigned long long& usum,
-                                              double& dsum, float& mn, float& mx) {
+                                              ff& fsum, float& mn, float& mx) {
     constexpr bool F32 = (KIND == K_F32_IDENT || KIND == K_F32_POLY3);
     const float ca = m.coef[0], cb = m.coef[1], cc = m.coef[2];
     if (!(m.flags & SF_DIRECT)) {
@@ -179,7 +180,7 @@ __device__ __forceinline__ void consume_chunk(const StageMeta& m, const char* st
                 mn = fminf(mn, fminf(fminf(y0, y1), fminf(y2, y3)));
                 mx = fmaxf(mx, fmaxf(fmaxf(y0, y1), fmaxf(y2, y3)));
             }
-            dsum += (double)cs;
+            fsum = ff_add_f(fsum, cs);
         } else {
 #pragma unroll
             for (int j = 0; j < IPT; ++j)
@@ -221,28 +222,27 @@ __device__ __forceinline__ void consume_chunk(const StageMeta& m, const char* st
                 if (ok[q]) usum += (unsigned long long)map_u32<KIND>(w[q]);
         }
     }
-    if constexpr (F32) dsum += (double)cs;
+    if constexpr (F32) fsum = ff_add_f(fsum, cs);
 }
 
 // Segment end: reduce among consumers, write the slot or the result, take the
 // task's ticket, fold if last.  Same order as stream_segment's epilogue.
 template <int CB, bool F32>
 __device__ __forceinline__ void segment_end(const KernelArgs& a, const StageMeta& m,
-                                            uint32_t tid, unsigned long long usum, double dsum,
+                                            uint32_t tid, unsigned long long usum, ff fsum,
                                             float mn, float mx, RedSmem& sm) {
-    if constexpr (F32) creduce_f<CB>(dsum, mn, mx, tid, sm);
-    else {
-        usum = csum_u64<CB>(usum, tid, sm);
-        dsum = (double)usum;
-    }
+    if constexpr (F32) creduce_ff<CB>(fsum, mn, mx, tid, sm);
+    else usum = csum_u64<CB>(usum, tid, sm);
     if (m.nseg == 1) {
         if (tid == 0)
-            write_result(m.result, usum, dsum, F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, m.n, m.kind);
+            write_result(m.result, usum, F32 ? ff_to_double(fsum) : (double)usum,
+                         F32 ? mn : 0.f, F32 ? mx : 0.f, SCL_OK, m.n, m.kind);
         return;
     }
     if (tid == 0) {
         StreamPartial* sp = a.spart + m.slot0 + m.local;
-        sp->s = dsum;
+        sp->shi = fsum.hi;
+        sp->slo = fsum.lo;
         sp->u = usum;
         sp->mn = mn;
         sp->mx = mx;
@@ -255,26 +255,24 @@ __device__ __forceinline__ void segment_end(const KernelArgs& a, const StageMeta
     named_sync<CB>();   // sm.flag may be rewritten by the next segment
     if (!last) return;
     __threadfence();
-    double fs = 0.0;
+    ff fs{0.f, 0.f};
     unsigned long long fu = 0;
     float fmn = CUDART_INF_F, fmx = -CUDART_INF_F;
     for (uint32_t s = tid; s < m.nseg; s += CB) {
         const StreamPartial* sp = a.spart + m.slot0 + s;
         if constexpr (F32) {
-            fs += __ldcg(&sp->s);
+            fs = ff_add(fs, ff{__ldcg(&sp->shi), __ldcg(&sp->slo)});
             fmn = fminf(fmn, __ldcg(&sp->mn));
             fmx = fmaxf(fmx, __ldcg(&sp->mx));
         } else {
             fu += __ldcg(reinterpret_cast<const unsigned long long*>(&sp->u));
         }
     }
-    if constexpr (F32) creduce_f<CB>(fs, fmn, fmx, tid, sm);
-    else {
-        fu = csum_u64<CB>(fu, tid, sm);
-        fs = (double)fu;
-    }
+    if constexpr (F32) creduce_ff<CB>(fs, fmn, fmx, tid, sm);
+    else fu = csum_u64<CB>(fu, tid, sm);
     if (tid == 0) {
-        write_result(m.result, fu, fs, F32 ? fmn : 0.f, F32 ? fmx : 0.f, SCL_OK, m.n, m.kind);
+        write_result(m.result, fu, F32 ? ff_to_double(fs) : (double)fu, F32 ? fmn : 0.f,
+                     F32 ? fmx : 0.f, SCL_OK, m.n, m.kind);
         a.tickets[m.task] = 0u;
     }
 }
@@ -390,7 +388,7 @@ __global__ void __launch_bounds__(CB + 32) k_stream_tma(const __grid_constant__ 
         const uint32_t lane = tid & 31;
         uint32_t s = 0, ph = 0;
         unsigned long long usum = 0;
-        double dsum = 0.0;
+        ff fsum{0.f, 0.f};
         float mn = CUDART_INF_F, mx = -CUDART_INF_F;
         for (;;) {
             if (!mbar_wait(full0 + 8 * s, ph, err)) break;
@@ -400,26 +398,26 @@ __global__ void __launch_bounds__(CB + 32) k_stream_tma(const __grid_constant__ 
             bool f32 = false;
             if constexpr (mask_has_u32(MASK)) {
                 if (m.kind == K_U32_IDENT)
-                    consume_chunk<CB, IPT, K_U32_IDENT>(m, stage, tid, usum, dsum, mn, mx);
+                    consume_chunk<CB, IPT, K_U32_IDENT>(m, stage, tid, usum, fsum, mn, mx);
                 else if (m.kind == K_U32_MIX32)
-                    consume_chunk<CB, IPT, K_U32_MIX32>(m, stage, tid, usum, dsum, mn, mx);
+                    consume_chunk<CB, IPT, K_U32_MIX32>(m, stage, tid, usum, fsum, mn, mx);
             }
             if constexpr (mask_has_f32(MASK)) {
                 if (m.kind == K_F32_IDENT) {
-                    consume_chunk<CB, IPT, K_F32_IDENT>(m, stage, tid, usum, dsum, mn, mx);
+                    consume_chunk<CB, IPT, K_F32_IDENT>(m, stage, tid, usum, fsum, mn, mx);
                     f32 = true;
                 } else if (m.kind == K_F32_POLY3) {
-                    consume_chunk<CB, IPT, K_F32_POLY3>(m, stage, tid, usum, dsum, mn, mx);
+                    consume_chunk<CB, IPT, K_F32_POLY3>(m, stage, tid, usum, fsum, mn, mx);
                     f32 = true;
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8 * s);
             if (m.flags & SF_LAST) {
-                if (f32) segment_end<CB, true>(a, m, tid, usum, dsum, mn, mx, sm);
-                else segment_end<CB, false>(a, m, tid, usum, dsum, mn, mx, sm);
+                if (f32) segment_end<CB, true>(a, m, tid, usum, fsum, mn, mx, sm);
+                else segment_end<CB, false>(a, m, tid, usum, fsum, mn, mx, sm);
                 usum = 0;
-                dsum = 0.0;
+                fsum = ff{0.f, 0.f};
                 mn = CUDART_INF_F;
                 mx = -CUDART_INF_F;
             }

@@ -479,14 +479,30 @@ int scl_server_stop(scl_ctx* ctx) {
     return SCL_OK;
 }
 
-int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s, uint32_t n,
-                      int64_t* latency_ns, scl_result* results) {
+// Open-loop replay: submits task i at its scheduled arrival on this thread
+// while a collector thread takes each result as soon as it is done, so the
+// map of finished results stays small however long the trace is.
+static int replay(scl_ctx* ctx, const scl_task* tasks, const scl_task_data* data,
+                  const double* arrival_s, uint32_t n, int64_t* latency_ns, scl_result* results) {
     Server* s = nullptr;
     SCL_TRY(srv_of(ctx, &s));
     if (n && (!tasks || !arrival_s)) return fail(SCL_E_INVALID, "null argument");
     std::vector<uint64_t> tickets(n, 0);
     std::vector<int64_t> sched(n);
     std::vector<int> sub_status(n, SCL_OK);
+    std::atomic<uint32_t> published{0};
+    std::thread collector([&] {
+        for (uint32_t i = 0; i < n; ++i) {
+            while (published.load(std::memory_order_acquire) <= i) std::this_thread::yield();
+            if (sub_status[i] != SCL_OK) continue;
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_done.wait(lk, [&] { return s->done.count(tickets[i]) > 0; });
+            auto it = s->done.find(tickets[i]);
+            if (latency_ns) latency_ns[i] = it->second.t_done - sched[i];
+            if (results) results[i] = it->second.r;
+            s->done.erase(it);
+        }
+    });
     const int64_t t0 = now_ns() + 1000000;   // start 1 ms from now
     for (uint32_t i = 0; i < n; ++i) {
         sched[i] = t0 + (int64_t)(arrival_s[i] * 1e9);
@@ -496,41 +512,57 @@ int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival
             else std::this_thread::yield();
             now = now_ns();
         }
-        Partition p;
-        {
-            std::lock_guard<std::recursive_mutex> g(ctx->mu);
-            const Partition* q = ctx->part(tasks[i].part);
-            if (!q) {
-                sub_status[i] = fail(SCL_E_INVALID, "task %u: unknown partition", i);
-                continue;
-            }
-            p = *q;
-        }
         SrvTask t;
         t.task = tasks[i];
         t.t_submit = sched[i];   // open loop: latency counts from the scheduled arrival
-        sub_status[i] = submit_common(ctx, std::move(t), p, &tickets[i]);
+        Partition p;
+        const scl_task_data* d = data ? &data[i] : nullptr;
+        if (d && d->host0) {
+            const scl_dtype dt = (scl_dtype)d->dtype;
+            if ((int)dt < 0 || dt > SCL_KV_I32_F32 || (dt == SCL_KV_I32_F32 && d->n && !d->host1)) {
+                sub_status[i] = fail(SCL_E_INVALID, "task %u: bad data description", i);
+            } else {
+                t.task.part = 0;
+                t.load = true;
+                t.host0 = d->host0;
+                t.host1 = d->host1;
+                t.dtype = dt;
+                t.n = d->n;
+                p = Partition{dt, d->n, nullptr, nullptr, nullptr};
+            }
+        } else {
+            std::lock_guard<std::recursive_mutex> g(ctx->mu);
+            const Partition* q = ctx->part(tasks[i].part);
+            if (!q) sub_status[i] = fail(SCL_E_INVALID, "task %u: unknown partition", i);
+            else p = *q;
+        }
+        if (sub_status[i] == SCL_OK) sub_status[i] = submit_common(ctx, std::move(t), p, &tickets[i]);
+        published.store(i + 1, std::memory_order_release);
     }
+    collector.join();
     int worst = SCL_OK;
     for (uint32_t i = 0; i < n; ++i) {
-        if (sub_status[i] != SCL_OK) {
-            if (latency_ns) latency_ns[i] = -1;
-            if (results) {
-                memset(&results[i], 0, sizeof results[i]);
-                results[i].status = sub_status[i];
-            }
-            if (worst == SCL_OK) worst = sub_status[i];
-            continue;
+        if (sub_status[i] == SCL_OK) continue;
+        if (latency_ns) latency_ns[i] = -1;
+        if (results) {
+            memset(&results[i], 0, sizeof results[i]);
+            results[i].status = sub_status[i];
         }
-        std::unique_lock<std::mutex> lk(s->mu);
-        s->cv_done.wait(lk, [&] { return s->done.count(tickets[i]) > 0; });
-        auto it = s->done.find(tickets[i]);
-        if (latency_ns) latency_ns[i] = it->second.t_done - sched[i];
-        if (results) results[i] = it->second.r;
-        s->done.erase(it);
+        if (worst == SCL_OK) worst = sub_status[i];
     }
     if (worst != SCL_OK) return fail(worst, "some tasks were not submitted");
     return SCL_OK;
+}
+
+int scl_server_replay(scl_ctx* ctx, const scl_task* tasks, const double* arrival_s, uint32_t n,
+                      int64_t* latency_ns, scl_result* results) {
+    return replay(ctx, tasks, nullptr, arrival_s, n, latency_ns, results);
+}
+
+int scl_server_replay_load(scl_ctx* ctx, const scl_task* tasks, const scl_task_data* data,
+                           const double* arrival_s, uint32_t n, int64_t* latency_ns,
+                           scl_result* results) {
+    return replay(ctx, tasks, data, arrival_s, n, latency_ns, results);
 }
 
 }  // extern "C"

@@ -116,7 +116,18 @@ class scl_task(ctypes.Structure):
                 ("reserved", ctypes.c_uint64)]
 
 
+class scl_task_data(ctypes.Structure):
+    _fields_ = [("host0", ctypes.c_void_p), ("host1", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_uint32)]
+
+
 assert ctypes.sizeof(scl_result) == 48 and ctypes.sizeof(scl_task) == 64
+assert ctypes.sizeof(scl_task_data) == 32
+
+# Bulk array of scl_task_data.
+TASK_DATA_DTYPE = np.dtype([("host0", "<u8"), ("host1", "<u8"), ("n", "<u8"), ("dtype", "<i4"),
+                            ("reserved", "<u4")])
+assert TASK_DATA_DTYPE.itemsize == 32
 
 # Result array dtype matching scl_result, for bulk reads.
 RESULT_DTYPE = np.dtype([("u64_sum", "<u8"), ("f64_sum", "<f8"), ("f32_sum", "<f4"),
@@ -155,6 +166,7 @@ _SIGS = {
     "scl_load_partition": ([_P, _P, ctypes.c_int, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_load_partition_kv": ([_P, _P, _P, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_wrap_device": ([_P, _P, _P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_alloc_partition": ([_P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_free_partition": ([_P, _u64], ctypes.c_int),
     "scl_reload_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
     "scl_partition_info": ([_P, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
@@ -198,6 +210,7 @@ _SIGS = {
     "scl_server_get_stats": ([_P, ctypes.POINTER(scl_server_stats)], ctypes.c_int),
     "scl_server_stop": ([_P], ctypes.c_int),
     "scl_server_replay": ([_P, _P, _P, _u32, _P, _P], ctypes.c_int),
+    "scl_server_replay_load": ([_P, _P, _P, _P, _u32, _P, _P], ctypes.c_int),
     "scl_devserver_start": ([_P, ctypes.POINTER(scl_devserver_config)], ctypes.c_int),
     "scl_devserver_submit": ([_P, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_devserver_poll": ([_P, _u64, ctypes.POINTER(scl_result)], ctypes.c_int),
@@ -297,6 +310,14 @@ def scl_load_partition_kv(ctx: int, keys, vals, n: int | None = None, stream: in
         n = int(keys.size if isinstance(keys, np.ndarray) else keys.numel())
     out = _u64()
     _check(lib.scl_load_partition_kv(ctx, _ptr(keys), _ptr(vals), n, stream, ctypes.byref(out)))
+    return out.value
+
+
+def scl_alloc_partition(ctx: int, dtype: int, n: int) -> int:
+    """An arena-resident partition whose contents the caller writes on the
+    device (pointers from scl_partition_info)."""
+    out = _u64()
+    _check(lib.scl_alloc_partition(ctx, dtype, n, ctypes.byref(out)))
     return out.value
 
 
@@ -535,8 +556,24 @@ def scl_server_replay(ctx: int, tasks: ctypes.Array, arrival_s: np.ndarray, n: i
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
     lat = np.zeros(max(1, n), dtype=np.int64)
     res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
-    st = lib.scl_server_replay(ctx, ctypes.cast(tasks, ctypes.c_void_p), arr.ctypes.data, n,
+    st = lib.scl_server_replay(ctx, _tasks_ptr(tasks), arr.ctypes.data, n,
                                lat.ctypes.data, res.ctypes.data)
+    if not allow_errors:
+        _check(st)
+    return lat[:n], res[:n]
+
+
+def scl_server_replay_load(ctx: int, tasks: ctypes.Array, data: np.ndarray,
+                           arrival_s: np.ndarray, n: int, allow_errors: bool = False):
+    """scl_server_replay where data[i] (TASK_DATA_DTYPE; host0 = 0 for a task on
+    its resident partition) gives the host arrays of tasks that bring new
+    data.  Returns (latency_ns int64[n], results RESULT_DTYPE[n])."""
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    d = np.ascontiguousarray(data, dtype=TASK_DATA_DTYPE)
+    lat = np.zeros(max(1, n), dtype=np.int64)
+    res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
+    st = lib.scl_server_replay_load(ctx, _tasks_ptr(tasks), d.ctypes.data,
+                                    arr.ctypes.data, n, lat.ctypes.data, res.ctypes.data)
     if not allow_errors:
         _check(st)
     return lat[:n], res[:n]
@@ -590,11 +627,26 @@ def scl_devserver_replay(ctx: int, tasks: ctypes.Array, arrival_s: np.ndarray, n
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
     lat = np.zeros(max(1, n), dtype=np.int64)
     res = np.zeros(max(1, n), dtype=RESULT_DTYPE)
-    st = lib.scl_devserver_replay(ctx, ctypes.cast(tasks, ctypes.c_void_p), arr.ctypes.data, n,
+    st = lib.scl_devserver_replay(ctx, _tasks_ptr(tasks), arr.ctypes.data, n,
                                   lat.ctypes.data, res.ctypes.data)
     if not allow_errors:
         _check(st)
     return lat[:n], res[:n]
+
+
+# Bulk array of scl_task (for traces of many tasks; replay functions take it).
+TASK_DTYPE = np.dtype([("part", "<u8"), ("kernel", "<i4"), ("reduce", "<i4"),
+                       ("num_keys", "<u4"), ("coef", "<f4", 3), ("counts_out", "<u8"),
+                       ("sums_out", "<u8"), ("sums64_out", "<u8"), ("reserved", "<u8")])
+assert TASK_DTYPE.itemsize == 64 and TASK_DTYPE.fields["counts_out"][1] == 32
+
+
+def _tasks_ptr(tasks):
+    if isinstance(tasks, np.ndarray):
+        if tasks.dtype != TASK_DTYPE or not tasks.flags.c_contiguous:
+            raise ValueError("tasks must be a contiguous TASK_DTYPE array")
+        return tasks.ctypes.data
+    return ctypes.cast(tasks, ctypes.c_void_p)
 
 
 def make_tasks(specs) -> ctypes.Array:

@@ -5,7 +5,7 @@ Tolerances (fixed by the workload definitions):
   * fp32 sums: |gpu - oracle| <= 1e-5 * |oracle| against the fp64 oracle, with
     an absolute floor of 1e-6 * sum|y| for tiny partitions whose sum cancels
     (the kernel's own error bound is a few 1e-7 * sum|y|: fp32 within a
-    thread's 4*IPT-element chunk, fp64 everywhere after);
+    thread's 4*IPT-element chunk, float-float pairs of about 44 bits after);
   * min / max: exact (same fp32 map in the same rounding on both sides).
 """
 from __future__ import annotations
