@@ -537,7 +537,9 @@ int scl_map_reduce_noalloc(const void* dev_in, scl_dtype dtype, uint64_t n,
  * entry, segment partials, keyed tables, and its input if it brings new data);
  * it enters the GPU queue when partitions resident in the arena + working sets
  * of admitted tasks + its own fit hbm_budget_bytes, otherwise it waits FIFO.
- * A task that can never fit is rejected with SCL_E_BUDGET. */
+ * A task that can never fit is rejected with SCL_E_BUDGET.  A task that brings
+ * new data is copied at admission and joins a launch once its copy has
+ * landed; tasks admitted after it do not wait for that copy. */
 typedef struct {
     int32_t inflight_batches;   /* launches on the GPU at once, one stream each
                                    (1..16; 0 = 4)                                  */

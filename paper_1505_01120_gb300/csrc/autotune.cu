@@ -240,7 +240,11 @@ int autotune(Ctx* c, const scl_autotune_config* cfg, cudaStream_t st, scl_autotu
             if (r != SCL_OK) continue;
             t[ci] = fam == M_F32 ? std::vector<double>{tb, ts, tm} : std::vector<double>{tb, ts};
         }
-        // objective: sum over probes of time / the best time on that probe
+        // objective: sum over probes of time / the best time on that probe.
+        // The keyed family's shape serves single keyed reduces and keyed-only
+        // batches, mostly large partitions (mixed batches take the fp32
+        // family's), so its large probe counts four times.
+        const double wbig = fam == M_KEYED ? 4.0 : 1.0;
         size_t best = cand.size();
         double best_score = 1e30, best_ms = 0;
         uint32_t tried = 0;
@@ -253,7 +257,7 @@ int autotune(Ctx* c, const scl_autotune_config* cfg, cudaStream_t st, scl_autotu
                 ++tried;
                 double score = 0, ms = 0;
                 for (size_t k = 0; k < t[ci].size(); ++k) {
-                    score += t[ci][k] / lo[k];
+                    score += (k == 0 ? wbig : 1.0) * t[ci][k] / lo[k];
                     ms += t[ci][k];
                 }
                 if (score < best_score) {

@@ -58,7 +58,7 @@ constexpr uint32_t kKeyedSmemBytes = (kKeyedTableWords + kKeyedHeadWords(512)) *
 // 2^(kFixCountBits + kFixTinyBits - 32) = 2^-18 of its magnitude.  Values
 // whose magnitude is outside the window (smaller, larger, non-finite) take
 // fp32 adds; the sign does not matter; zeros add nothing.
-constexpr uint32_t kFixCountBits = 9;
+constexpr uint32_t kFixCountBits = 9;   // also keeps |round(v * 2^F)| <= 2^22 (exact FMA rounding)
 constexpr uint32_t kFixTinyBits = 5;
 constexpr uint64_t kFixWindow = 65536;        // pairs per window, a multiple of every chunk
 constexpr uint64_t kFixMinPairs = 16384;      // shorter pieces use the fp32 table only

@@ -381,6 +381,14 @@ struct FixWin {
     uint32_t lo, span;
 };
 
+// round(v * scale) for |v * scale| <= 2^22 (scale a power of two, so the
+// product is exact): adding 1.5 * 2^23 in the same rounding step leaves the
+// integer, rounded to nearest even, in the low mantissa bits.  One fp32 FMA
+// instead of a conversion on the slower XU pipe.
+__device__ __forceinline__ int32_t fix_round(float v, float scale) {
+    return __float_as_int(__fmaf_rn(v, scale, 12582912.0f)) - 0x4B400000;
+}
+
 // As keyed_add, with values inside the window added to the int32 sums.
 template <bool HASHED>
 __device__ __forceinline__ void keyed_add_fix(uint32_t k, uint32_t v, uint32_t nk, uint32_t* cnt,
@@ -393,7 +401,7 @@ __device__ __forceinline__ void keyed_add_fix(uint32_t k, uint32_t v, uint32_t n
         if (!HASHED && k < kKeyedHead)
             atomicAdd(&head[k], __uint_as_float(v));
         else if (ab - w.lo < w.span)
-            atomicAdd(&isum[k], __float2int_rn(__uint_as_float(v) * w.scale));
+            atomicAdd(&isum[k], fix_round(__uint_as_float(v), w.scale));
         else if (ab != 0u)   // a zero of either sign adds nothing
             atomicAdd(&sum[k], __uint_as_float(v));
     } else {
@@ -492,23 +500,26 @@ __device__ __forceinline__ uint32_t keyed_pass(const DevTask& t, uint64_t b, uin
     return 0u;
 }
 
+// Zeroes words [0, n) of a shared array, 16 bytes per store where it can.
+template <int BLOCK>
+__device__ __forceinline__ void smem_zero(uint32_t* p, uint32_t n) {
+    const uint32_t n4 = n / 4;
+    for (uint32_t i = threadIdx.x; i < n4; i += BLOCK)
+        reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t i = n4 * 4 + threadIdx.x; i < n; i += BLOCK) p[i] = 0u;
+}
+
 // Zeroes the count and fp32 sum of ids [0, nk) and the head copies (and, with
 // FIX, the int32 sums and count snapshots).  Call between barriers.
 template <int BLOCK, bool HASHED, bool FIX>
 __device__ __forceinline__ void keyed_zero(uint32_t* tab, uint32_t nk) {
-    uint32_t* cnt = tab;
-    float* sum = reinterpret_cast<float*>(tab + kMaxKeys);
-    float* heads = reinterpret_cast<float*>(tab + kKeyedTableWords);
-    for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
-        cnt[k] = 0u;
-        sum[k] = 0.f;
-        if constexpr (FIX) {
-            reinterpret_cast<int32_t*>(reinterpret_cast<char*>(tab) + kFixSumOffset)[k] = 0;
-            reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixSnapOffset)[k] = 0u;
-        }
+    smem_zero<BLOCK>(tab, nk);
+    smem_zero<BLOCK>(tab + kMaxKeys, nk);
+    if constexpr (FIX) {
+        smem_zero<BLOCK>(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixSumOffset), nk);
+        smem_zero<BLOCK>(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(tab) + kFixSnapOffset), nk);
     }
-    if (!HASHED)
-        for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(BLOCK); i += BLOCK) heads[i] = 0.f;
+    if (!HASHED) smem_zero<BLOCK>(tab + kKeyedTableWords, kKeyedHeadWords(BLOCK));
 }
 
 // Largest finite |v| (as a bit pattern) over this thread's pairs of the first
@@ -617,7 +628,24 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
     if (t.nseg == 1) {
         unsigned long long ctot = 0;
         ff stot{0.f, 0.f};
-        for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+        // 16 bytes per access where the outputs allow it (uniform branch)
+        const bool vec = ((reinterpret_cast<uintptr_t>(t.counts_out) |
+                           reinterpret_cast<uintptr_t>(t.sums_out) |
+                           reinterpret_cast<uintptr_t>(t.sums64_out)) & 15u) == 0;
+        const uint32_t nv = vec ? nk / 4 : 0u;
+        for (uint32_t q = threadIdx.x; q < nv; q += BLOCK) {
+            const uint4 c = reinterpret_cast<const uint4*>(cnt)[q];
+            const float4 s = reinterpret_cast<const float4*>(sum)[q];
+            reinterpret_cast<uint4*>(t.counts_out)[q] = c;
+            reinterpret_cast<float4*>(t.sums_out)[q] = s;
+            if (t.sums64_out) {
+                reinterpret_cast<double2*>(t.sums64_out)[2 * q] = make_double2(s.x, s.y);
+                reinterpret_cast<double2*>(t.sums64_out)[2 * q + 1] = make_double2(s.z, s.w);
+            }
+            ctot += (unsigned long long)c.x + c.y + c.z + c.w;
+            stot = ff_add_f(ff_add_f(ff_add_f(ff_add_f(stot, s.x), s.y), s.z), s.w);
+        }
+        for (uint32_t k = nv * 4 + threadIdx.x; k < nk; k += BLOCK) {
             const uint32_t c = cnt[k];
             const float s = sum[k];
             t.counts_out[k] = c;
@@ -636,7 +664,13 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
         }
     } else {
         uint32_t* dst = a.kpart + (size_t)(t.slot0 + slot) * kKeyedTableWords;
-        for (uint32_t k = threadIdx.x; k < nk; k += BLOCK) {
+        const uint32_t nv = nk / 4;
+        for (uint32_t q = threadIdx.x; q < nv; q += BLOCK) {
+            __stcg(reinterpret_cast<uint4*>(dst) + q, reinterpret_cast<const uint4*>(cnt)[q]);
+            __stcg(reinterpret_cast<uint4*>(dst + kMaxKeys) + q,
+                   reinterpret_cast<const uint4*>(sum)[q]);
+        }
+        for (uint32_t k = nv * 4 + threadIdx.x; k < nk; k += BLOCK) {
             __stcg(dst + k, cnt[k]);
             __stcg(dst + kMaxKeys + k, __float_as_uint(sum[k]));
         }

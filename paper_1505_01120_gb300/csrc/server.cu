@@ -211,12 +211,33 @@ void Server::batcher_loop() {
         });
         if (admitted.empty()) break;   // stopping, nothing left to launch
         Slot& s = *free_slot;
-        s.busy = true;
-        const size_t take = std::min<size_t>(admitted.size(), cfg.max_batch_tasks);
-        s.tasks.assign(std::make_move_iterator(admitted.begin()),
-                       std::make_move_iterator(admitted.begin() + take));
-        admitted.erase(admitted.begin(), admitted.begin() + take);
+        // Take, in admission order, the tasks whose input is on the device: a
+        // task that brings new data joins a launch once its copy has landed,
+        // so a large copy does not hold back the tasks admitted after it.
+        // Only a bounded prefix is looked at, so a long backlog costs nothing.
+        s.tasks.clear();
+        std::vector<SrvTask> pending;
+        size_t scanned = 0;
+        while (!admitted.empty() && s.tasks.size() < cfg.max_batch_tasks &&
+               scanned < (size_t)cfg.max_batch_tasks + 256) {
+            SrvTask& t = admitted.front();
+            if (!t.ready || cudaEventQuery(t.ready) != cudaErrorNotReady)
+                s.tasks.push_back(std::move(t));
+            else
+                pending.push_back(std::move(t));
+            admitted.pop_front();
+            ++scanned;
+        }
+        for (auto it = pending.rbegin(); it != pending.rend(); ++it)
+            admitted.push_front(std::move(*it));
         admitted_n.store(admitted.size(), std::memory_order_release);
+        if (s.tasks.empty()) {   // only copies in flight: look again shortly
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(5));
+            lk.lock();
+            continue;
+        }
+        s.busy = true;
         lk.unlock();
         const int st = launch_slot(s);
         lk.lock();

@@ -6,7 +6,10 @@
 // otherwise it waits, FIFO.  A batcher thread packs every admitted task (up
 // to max_batch_tasks) into one persistent launch as soon as one of K
 // in-flight slots is free, so work arriving while other batches run joins
-// the next launch and overlaps with them on the device.  A completion thread
+// the next launch and overlaps with them on the device; a task that brings
+// new data joins a launch once its host-to-device copy has landed (launch
+// order is admission order among the tasks whose input is on the device).
+// A completion thread
 // polls each slot's event, stamps completion times, publishes results,
 // returns budget and admits waiting tasks.  With max_batch_tasks = 1 and one
 // slot it is the unbatched baseline: one launch per task, FIFO.
