@@ -425,27 +425,12 @@ __global__ void __launch_bounds__(BLOCK, 3) k_radix_scatter(const __grid_constan
     if (bad) atomicOr(a.bad, bad);
 }
 
-// One pair of pass 4: the count, then the value to the head copy (ids below
-// kKeyedHead), to the int32 sums (inside the window, FIX), or to the fp32
-// table.
-__device__ __forceinline__ void radix_add(uint32_t kk, uint32_t v, uint32_t* hc, float* hs,
-                                          float* my, int32_t* hq, const FixWin& w, bool fix) {
-    atomicAdd(&hc[kk], 1u);
-    const uint32_t ab = v & 0x7fffffffu;
-    if (kk < kKeyedHead) atomicAdd(&my[kk], __uint_as_float(v));
-    else if (fix && ab - w.lo < w.span) atomicAdd(&hq[kk], fix_round(__uint_as_float(v), w.scale));
-    else if (ab != 0u) atomicAdd(&hs[kk], __uint_as_float(v));
-}
-
 // Pass 4: the grouped pairs split over the grid in even shares of cost
 // (radix.h); each bucket segment of a CTA's share is accumulated in the
-// shared table of 2^LOG_T ids, with the head copies of its first ids, and
-// written out every kLargePiece pairs (so fp32 partial sums stay short).
-// Within a piece, values inside the fixed-point window of the piece's first
-// loads go to int32 sums (FixWin, as in the keyed-only kernel); a piece in
-// which an id other than the head ids took 2^kFixCountBits pairs or more runs
-// again on the fp32 table alone.  The table is zeroed once; each flush clears
-// the entries it writes out and the head copies it folds.
+// shared table of 2^LOG_T ids, with the head copies of its first ids (flushed
+// every kLargePiece pairs so fp32 partial sums stay short), and written out.
+// The table is zeroed once; each flush clears the entries it writes out and
+// the head copies it folds.
 template <int BLOCK, int LOG_T>
 __global__ void __launch_bounds__(BLOCK) k_radix_reduce(const __grid_constant__ RadixArgs a) {
     constexpr uint32_t T = 1u << LOG_T;
@@ -455,15 +440,13 @@ __global__ void __launch_bounds__(BLOCK) k_radix_reduce(const __grid_constant__ 
     uint32_t* hc = smem;                                   // [T] counts
     float* hs = reinterpret_cast<float*>(smem + T);        // [T] fp32 sums
     float* head = hs + T;                                  // [BLOCK / 32 * classes][HP]
-    int32_t* hq = reinterpret_cast<int32_t*>(smem + 2 * T + kKeyedHeadWords(BLOCK));  // [T]
-    uint32_t* wmax = reinterpret_cast<uint32_t*>(hq + T);  // [BLOCK / 32]
     float* my = head + ((threadIdx.x >> 5) * kKeyedHeadClasses +
                         (threadIdx.x & (kKeyedHeadClasses - 1))) * HP;
     const uint64_t ctot = __ldg(&a.bcost[a.nb]);
     const uint64_t clo = ctot * blockIdx.x / gridDim.x;
     const uint64_t chi = ctot * (blockIdx.x + 1) / gridDim.x;
     if (clo >= chi) return;
-    for (uint32_t i = threadIdx.x; i < 3 * T + kKeyedHeadWords(BLOCK); i += BLOCK) smem[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < 2 * T + kKeyedHeadWords(BLOCK); i += BLOCK) smem[i] = 0u;
     __syncthreads();
     // the bucket holding cost position clo: the last b with bcost[b] <= clo
     uint32_t bl = 0, bh = a.nb - 1;
@@ -490,60 +473,31 @@ __global__ void __launch_bounds__(BLOCK) k_radix_reduce(const __grid_constant__ 
             const uint64_t p1 = min(p0 + kLargePiece, bbeg + j1);
             // pairs [p0, p1) as 16-byte loads of two pairs each
             const uint64_t q0 = p0 >> 1, q1 = (p1 + 1) >> 1;
-            // the piece's window, from the largest finite value among the
-            // pairs of each thread's first loads (read again from L2 below)
-            uint32_t m = 0;
+            for (uint64_t q = q0 + threadIdx.x; q < q1; q += (uint64_t)BLOCK * 4) {
+                uint4 w[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t qq = q0 + threadIdx.x + (uint64_t)j * BLOCK;
-                if (qq < q1) {
-                    const uint4 w = ld_stream_v4(a.bk + qq * 4);
-                    const uint32_t a0 = w.y & 0x7fffffffu, a1 = w.w & 0x7fffffffu;
-                    if (2 * qq >= p0 && a0 < 0x7f800000u) m = max(m, a0);
-                    if (2 * qq + 1 < p1 && a1 < 0x7f800000u) m = max(m, a1);
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t qq = q + (uint64_t)j * BLOCK;
+                    w[j] = qq < q1 ? ld_stream_v4(a.bk + qq * 4) : make_uint4(0u, 0u, 0u, 0u);
                 }
-            }
-            m = __reduce_max_sync(0xffffffffu, m);
-            if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
-            __syncthreads();
-            uint32_t mm = 0;
 #pragma unroll
-            for (int q = 0; q < BLOCK / 32; ++q) mm = max(mm, wmax[q]);
-            FixWin fw{0.f, 0.f, 0u, 0u};
-            bool fix = fix_window(mm, &fw);
-            for (;;) {
-                for (uint64_t q = q0 + threadIdx.x; q < q1; q += (uint64_t)BLOCK * 4) {
-                    uint4 w[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint64_t qq = q + (uint64_t)j * BLOCK;
-                        w[j] = qq < q1 ? ld_stream_v4(a.bk + qq * 4) : make_uint4(0u, 0u, 0u, 0u);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint64_t qq = q + (uint64_t)j * BLOCK;
-                        if (qq < q1) {
-                            if (2 * qq >= p0) radix_add(w[j].x & (T - 1), w[j].y, hc, hs, my, hq, fw, fix);
-                            if (2 * qq + 1 < p1) radix_add(w[j].z & (T - 1), w[j].w, hc, hs, my, hq, fw, fix);
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t qq = q + (uint64_t)j * BLOCK;
+                    if (qq < q1) {
+                        if (2 * qq >= p0) {
+                            const uint32_t kk = w[j].x & (T - 1);
+                            atomicAdd(&hc[kk], 1u);
+                            atomicAdd(kk < kKeyedHead ? &my[kk] : &hs[kk], __uint_as_float(w[j].y));
+                        }
+                        if (2 * qq + 1 < p1) {
+                            const uint32_t kk = w[j].z & (T - 1);
+                            atomicAdd(&hc[kk], 1u);
+                            atomicAdd(kk < kKeyedHead ? &my[kk] : &hs[kk], __uint_as_float(w[j].w));
                         }
                     }
                 }
-                __syncthreads();
-                if (!fix) break;
-                uint32_t over = 0;
-                for (uint32_t i = kKeyedHead + threadIdx.x; i < hot; i += BLOCK)
-                    over |= (uint32_t)(hc[i] >= (1u << kFixCountBits));
-                if (!__syncthreads_or((int)over)) break;
-                // an int32 sum may have wrapped: the piece again, fp32 only
-                for (uint32_t i = threadIdx.x; i < hot; i += BLOCK) {
-                    hc[i] = 0u;
-                    hs[i] = 0.f;
-                    hq[i] = 0;
-                }
-                for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(BLOCK); i += BLOCK) head[i] = 0.f;
-                __syncthreads();
-                fix = false;
             }
+            __syncthreads();
             fold_head_copies(head, hs, min(hot, kKeyedHead));
             __syncthreads();
             uint32_t* cnt = a.counts + (size_t)b * T;
@@ -551,17 +505,16 @@ __global__ void __launch_bounds__(BLOCK) k_radix_reduce(const __grid_constant__ 
             for (uint32_t i = threadIdx.x; i < hot; i += BLOCK) {
                 const uint32_t c = hc[i];
                 if (c) {
-                    const double t = (double)hs[i] + (double)hq[i] * (double)fw.inv;
+                    const float t = hs[i];
                     if (single) {
                         cnt[i] = c;
-                        sum[i] = t;
+                        sum[i] = (double)t;
                     } else {
                         atomicAdd(&cnt[i], c);
-                        atomicAdd(&sum[i], t);
+                        atomicAdd(&sum[i], (double)t);
                     }
                     hc[i] = 0u;
                     hs[i] = 0.f;
-                    hq[i] = 0;
                 }
             }
             __syncthreads();   // the table is clean for the next piece

@@ -34,10 +34,7 @@
 //      of a skewed key set do not land on a few CTAs); a CTA accumulates each
 //      bucket segment of its share in the shared table and writes it out
 //      (plain stores when it holds the whole bucket, global atomics
-//      otherwise).  Each piece of a segment (kLargePiece pairs) adds the
-//      values inside its fixed-point window as int32 (as the keyed-only
-//      kernel does); an id that took 2^kFixCountBits pairs or more in the
-//      piece makes the piece run again on the fp32 table.
+//      otherwise).
 // A finishing pass (the one of the direct path) rounds the fp64 sums to fp32
 // and forms the totals.
 #pragma once
@@ -144,15 +141,13 @@ __host__ __device__ constexpr uint32_t radix_scatter_smem(uint32_t nb, bool hot)
 __host__ __device__ inline uint32_t radix_hist_smem(uint32_t nb) { return (nb + 1) * 4; }
 
 // The reduce kernel per bucket width: threads per CTA and dynamic shared
-// memory (count and fp32 sum per id, the head copies, the int32 sums of the
-// fixed-point window per id, one word per warp).
+// memory (count and fp32 sum per id, then the head copies).
 // (8192 ids: 2 CTAs of 1024 threads per SM beat 3 of 512 by 3% on GB300.)
 __host__ __device__ constexpr uint32_t radix_reduce_block(uint32_t log_t) {
     return log_t >= 13 ? 1024u : 512u;
 }
 __host__ __device__ constexpr uint32_t radix_reduce_smem(uint32_t log_t) {
-    return ((3u << log_t) + kKeyedHeadWords(radix_reduce_block(log_t)) +
-            radix_reduce_block(log_t) / 32) * 4;
+    return ((2u << log_t) + kKeyedHeadWords(radix_reduce_block(log_t))) * 4;
 }
 
 // Limits the kernels rely on: cost starts fit 32 bits at the largest

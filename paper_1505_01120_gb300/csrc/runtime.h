@@ -193,10 +193,11 @@ struct Ctx {
     std::recursive_mutex mu;
     std::unordered_map<uint64_t, Partition> parts;
     uint64_t next_part = 1;
-    // Defaults: the fastest shapes measured on GB300 (vector-load kernels;
-    // the keyed kernel is bound by shared-memory atomics, not the shape).
+    // Defaults: the fastest shapes measured on GB300 (vector-load kernels):
+    // 256x8 for the streaming families and the mixed kernel; 512x4 for the
+    // keyed-only kernel (two CTAs of 72 KB per SM, 32 warps).
     Shape shape[M_NUM] = {Shape{256, 8, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0},
-                          Shape{256, 4, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0}};
+                          Shape{512, 4, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0}};
     std::map<const void*, int> occ_cache;
     // Scratch of single-partition launches, one per stream, so that launches
     // on different streams may overlap on the device.
