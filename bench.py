@@ -975,6 +975,7 @@ def run_ncu_case(args):
     the configs, a few launches, a 3 GiB arena): 'keyed' = 16 x 16 Mi pairs
     keyed count+sum; 'tree' = vector-add ReduceCL of 64 x 4 Mi fp32 arrays;
     'batch' = the 10,000-task uneven batch (2.79 GB), one launch per step;
+    'batch-f32' = its 3,289 fp32 poly3 tasks alone;
     'mix32' = 256 x 1 Mi uint32 mix32 sums in one launch; 'map' = poly3 over
     256 Mi fp32 with the output materialised; 'large' = keyed count+sum over
     2^20 keys, 64 Mi uniform pairs."""
@@ -1002,8 +1003,10 @@ def run_ncu_case(args):
                               sums64_out=base + 32768))
         b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), 16)
         fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
-    elif args.ncu_case == "batch":
-        _specs, tasks, _parts, _nb, _bufs = build_batch(torch, scl, ctx)
+    elif args.ncu_case in ("batch", "batch-f32"):
+        specs, tasks, _parts, _nb, _bufs = build_batch(torch, scl, ctx)
+        if args.ncu_case == "batch-f32":   # the fp32 poly3 tasks of the batch only
+            tasks = [t for t, s_ in zip(tasks, specs) if s_.kind == synth.KIND_POLY3]
         b = scl.scl_batch_create(ctx.handle, scl.make_tasks(tasks), len(tasks))
         fn = lambda: scl.scl_batch_launch(b, st)  # noqa: E731
     elif args.ncu_case == "mix32":
@@ -1324,7 +1327,8 @@ def main():
                     help="with --ncu-case headline: run the fp32 family on the TMA "
                          "bulk-copy pipeline (256 x 4, 4 stages)")
     ap.add_argument("--ncu-case", nargs="?", const="headline", default=None,
-                    choices=["headline", "keyed", "tree", "batch", "mix32", "map", "large"],
+                    choices=["headline", "keyed", "tree", "batch", "batch-f32", "mix32", "map",
+                             "large"],
                     help="profiler case: one workload's kernel only, small arena, no JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1333,7 +1337,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.ncu_case in ("keyed", "tree", "batch", "mix32", "map", "large"):
+    elif args.ncu_case in ("keyed", "tree", "batch", "batch-f32", "mix32", "map", "large"):
         run_ncu_case(args)
     else:
         run_ours(args, rank, world)
