@@ -802,8 +802,9 @@ def keyed_zipf_config(torch, scl, ctx, stream, pk: float) -> dict:
 
 
 def keyed_large_config(torch, scl, ctx, stream, pk: float) -> dict:
-    """Keyed count+sum over 2^20 keys, 64 Mi pairs (the bucket-partitioned
-    path): uniform keys, and Zipf(1.2) keys numbered by frequency."""
+    """Keyed count+sum over 2^20 keys, 64 Mi pairs: uniform keys, and
+    Zipf(1.2) keys numbered by frequency; the automatic path (packed direct)
+    and the bucket-partitioned path."""
     import oracle
     st = stream.cuda_stream
     nk, n = 1 << 20, 1 << 26
@@ -821,9 +822,17 @@ def keyed_large_config(torch, scl, ctx, stream, pk: float) -> dict:
             ctx.handle, p, nk, dc, ds, d64, dr, stream=st), 10)
         ocnt, _, _ = oracle.keyed_count_sum(keys, vals, nk)
         exact = bool(np.array_equal(dc.cpu().numpy().view(np.uint32), ocnt))
+        # the bucket-partitioned path on the same pairs, for comparison
+        scl.scl_set_large_path(ctx.handle, scl.SCL_LARGE_PARTITIONED)
+        ms_part = time_device(torch, stream, lambda: scl.scl_keyed_reduce_large_async(
+            ctx.handle, p, nk, dc, ds, d64, dr, stream=st), 10)
+        exact_part = bool(np.array_equal(dc.cpu().numpy().view(np.uint32), ocnt))
+        scl.scl_set_large_path(ctx.handle, scl.SCL_LARGE_AUTO)
         scl.scl_free_partition(ctx.handle, p)
-        out[name] = {"gbs": 8 * n / ms / 1e6, "frac_of_hbm": 8 * n / ms / 1e6 / pk, "ms": ms,
-                     "pairs_per_s": n / ms * 1e3, "counts_exact": exact}
+        out[name] = {"path": "packed direct (automatic choice)",
+                     "gbs": 8 * n / ms / 1e6, "frac_of_hbm": 8 * n / ms / 1e6 / pk, "ms": ms,
+                     "pairs_per_s": n / ms * 1e3, "counts_exact": exact,
+                     "partitioned_ms": ms_part, "partitioned_counts_exact": exact_part}
     return out
 
 

@@ -302,7 +302,19 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
 #define SCL_MAX_LARGE_KEYS 16777216u
 
 /* The keyed reduce for key spaces larger than 4096 (a WordCount-size
- * vocabulary, Sec. 3.2.3).  num_keys in [1, SCL_MAX_LARGE_KEYS].  Two paths:
+ * vocabulary, Sec. 3.2.3).  num_keys in [1, SCL_MAX_LARGE_KEYS].  Three paths
+ * (scl_set_large_path chooses; by default packed from 2^17 to 2^22 keys,
+ * else bucket-partitioned, else direct):
+ *   - packed direct, for up to 2^22 keys: ids below 4096 go to a per-block
+ *     shared-memory table; every other pair whose value is non-negative and
+ *     inside a window [B/256, B) -- B the power of two above the largest value
+ *     among the partition's first 65,536 -- takes one 64-bit integer add in
+ *     L2 to a packed word per id (count in bits 40..63, round(v * 2^F) in
+ *     bits 0..39, rounding error at most 2^-18 of v); other values take the
+ *     direct path's two atomics.  If a packed word overflowed (an id with more
+ *     than 32,768 packed pairs or 2^24 pairs), the call redoes itself on the
+ *     device without packing (the result is the same; it takes longer).  Needs
+ *     8 B per key from the arena;
  *   - bucket-partitioned, for partitions of 2^20 to 2^31 - 1 pairs whose key
  *     and value arrays are 16-byte aligned, over more than 4096 keys: the
  *     pairs are grouped by bucket (4096 to 16384 consecutive ids) in a
@@ -315,7 +327,7 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
  *     below 4096 (the frequent ids when words are numbered by frequency) go
  *     to a per-block shared-memory table, every other key straight to global
  *     atomics.
- * Both yield the same tables.  HOST outputs of num_keys entries; sums_out is
+ * All yield the same tables.  HOST outputs of num_keys entries; sums_out is
  * the fp64 sum rounded to fp32.  Counts are exact; sums are fp32 partial sums
  * of at most 131,072 pairs per block and key added in fp64, within 1e-5 of an
  * fp64 fold (atomic order varies between runs).  Uses temporary device
@@ -327,6 +339,20 @@ int scl_keyed_reduce_hashed(scl_ctx* ctx, scl_part part, uint32_t num_keys,
 int scl_keyed_reduce_large(scl_ctx* ctx, scl_part part, uint32_t num_keys, void* stream,
                            uint32_t* counts_out, float* sums_out, double* sums64_out,
                            scl_result* result);
+
+/* Path of the large-key reduce.  A path that cannot run (partitioned: an
+ * unaligned or short partition, or no arena room; packed: more than 2^22
+ * keys, or no arena room) falls back to the direct kernel. */
+typedef enum {
+    SCL_LARGE_AUTO = 0,          /* packed for 2^17 to 2^22 keys, else partitioned */
+    SCL_LARGE_PACKED = 1,
+    SCL_LARGE_PARTITIONED = 2,
+    SCL_LARGE_DIRECT = 3         /* the direct kernel without packing */
+} scl_large_path;
+
+/* Choose the path of this context's later large-key calls.
+ * Errors: SCL_E_INVALID (unknown path). */
+int scl_set_large_path(scl_ctx* ctx, scl_large_path path);
 
 /* Enqueue-only form on DEVICE tables the caller owns: counts_dev (uint32),
  * sums_dev (float) and sums64_dev (double, required: it is the accumulator),

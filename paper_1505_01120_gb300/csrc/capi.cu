@@ -586,10 +586,12 @@ static int launch_radix(Ctx* c, Scratch& sc, const Partition& p, uint32_t nk, ui
     return SCL_OK;
 }
 
-// Large key spaces: the bucket-partitioned path for partitions of at least
-// kRadixMinPairs aligned pairs over more than kMaxKeys keys, when its tables
-// fit the arena; otherwise the direct kernel (shared table for ids below
-// kMaxKeys, global atomics for the rest).  Then the finishing pass.
+// Large key spaces: kMinPackedKeys to kMaxPackedKeys keys, the direct kernel with packed
+// L2 words (shared table for ids below kMaxKeys, one 64-bit add per other
+// pair, count / fp64 adds for values outside the window) and its repair
+// chain; above, the bucket-partitioned path for partitions of at least
+// kRadixMinPairs aligned pairs when its tables fit the arena; otherwise the
+// direct kernel without packing.  Then the finishing pass.
 static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uint32_t* counts,
                               float* sums, double* sums64, scl_result* res, cudaStream_t st,
                               void** call_tmp) {
@@ -612,19 +614,38 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
     SCL_CUDA(cudaMemsetAsync(a.bad, 0, 4, st));
     void* params[] = {&a};
     bool done = false;   // the partitioned path zeroes the output tables in its first kernel
-    if (a.aligned && nk > kMaxKeys && p.n >= kRadixMinPairs && p.n <= kRadixMaxPairs)
+    // Key spaces of kMinPackedKeys to kMaxPackedKeys: the direct kernel with
+    // packed L2 words (one 64-bit add per pair); others: the bucket-
+    // partitioned path when its tables fit the arena.
+    const int path = ctx->large_path;
+    const bool packed = nk > kMaxKeys && nk <= kMaxPackedKeys && p.n &&
+                        ((path == SCL_LARGE_AUTO && nk >= kMinPackedKeys) ||
+                         path == SCL_LARGE_PACKED);
+    if (!packed && (path == SCL_LARGE_AUTO || path == SCL_LARGE_PARTITIONED) && a.aligned &&
+        nk > kMaxKeys && p.n >= kRadixMinPairs && p.n <= kRadixMaxPairs)
         SCL_TRY(launch_radix(ctx, sc, p, nk, counts, sums64, a.bad, st, call_tmp, &done));
     if (!done) {
         SCL_CUDA(cudaMemsetAsync(counts, 0, (size_t)nk * 4, st));
         SCL_CUDA(cudaMemsetAsync(sums64, 0, (size_t)nk * 8, st));
     }
+    if (packed) {
+        char* t = static_cast<char*>(radix_tables(ctx, sc, align_up((size_t)nk * 8) + 256,
+                                                  call_tmp));
+        if (t) {   // else the direct kernel without packing
+            a.packed = reinterpret_cast<unsigned long long*>(t);
+            a.fix = reinterpret_cast<LargeFix*>(t + align_up((size_t)nk * 8));
+            SCL_CUDA(cudaMemsetAsync(a.packed, 0, (size_t)nk * 8, st));
+            SCL_CUDA(cudaLaunchKernel(large_scale_fn(), dim3(1), dim3(256), params, 0, st));
+            count_launches(1);
+        }
+    }
+    const void* fn = large_keyed_kernel_fn(a.aligned);
+    int nb = 0;
+    SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0));
+    const uint64_t pieces = (p.n + kDirectPiece - 1) / kDirectPiece;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(pieces, (uint64_t)ctx->sms * std::max(nb, 1)));
     if (p.n && !done) {
-        const void* fn = large_keyed_kernel_fn(a.aligned);
-        int nb = 0;
-        SCL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0));
-        const uint64_t pieces = (p.n + kLargePiece - 1) / kLargePiece;
-        const uint32_t grid = (uint32_t)std::max<uint64_t>(
-            1, std::min<uint64_t>(pieces, (uint64_t)ctx->sms * std::max(nb, 1)));
         SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(256), params, 0, st));
         count_launches(1);
     }
@@ -634,6 +655,29 @@ static int launch_large_keyed(scl_ctx* ctx, const Partition& p, uint32_t nk, uin
         1, std::min<uint64_t>(((uint64_t)nk + 255) / 256, (uint64_t)ctx->sms * 2));
     SCL_CUDA(cudaLaunchKernel(large_keyed_finish_fn(), dim3(fgrid), dim3(256), params, 0, st));
     count_launches(1);
+    if (a.packed) {
+        // The repair chain: each kernel returns at once unless the finishing
+        // pass found that a packed word overflowed; then the outputs are
+        // zeroed and the call is done again without packing.
+        LargeKeyedArgs r = a;
+        r.packed = nullptr;
+        r.guard = 1u;
+        void* rparams[] = {&r};
+        const uint32_t zgrid = (uint32_t)std::max<uint64_t>(
+            1, std::min<uint64_t>(((uint64_t)nk + 255) / 256, (uint64_t)ctx->sms * 4));
+        SCL_CUDA(cudaLaunchKernel(large_repair_zero_fn(), dim3(zgrid), dim3(256), rparams, 0, st));
+        SCL_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(256), rparams, 0, st));
+        SCL_CUDA(cudaLaunchKernel(large_keyed_finish_fn(), dim3(fgrid), dim3(256), rparams, 0, st));
+        count_launches(3);
+    }
+    return SCL_OK;
+}
+
+int scl_set_large_path(scl_ctx* ctx, scl_large_path path) {
+    CTX_ENTER(ctx);
+    if ((int)path < SCL_LARGE_AUTO || (int)path > SCL_LARGE_DIRECT)
+        return fail(SCL_E_INVALID, "unknown large-key path %d", (int)path);
+    ctx->large_path = (int)path;
     return SCL_OK;
 }
 

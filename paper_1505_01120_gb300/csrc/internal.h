@@ -207,6 +207,40 @@ struct TreeArgs {
 // go straight to global count / fp64 sum atomics.
 constexpr uint32_t kMaxLargeKeys = 1u << 24;
 constexpr uint64_t kLargePiece = 131072;
+// Pairs per piece of the direct kernel (64 Mi pairs over 2^20 uniform keys,
+// packed: 0.479 ms at 131,072, 0.454 at 32,768 -- more CTAs keep more L2 adds
+// in flight -- 0.448 at 16,384, where skewed keys lose to table flushes).
+constexpr uint64_t kDirectPiece = 32768;
+
+// Packed L2 accumulators of the direct path (num_keys up to kMaxPackedKeys):
+// one 64-bit word per id, count in bits 40..63 and a fixed-point sum in bits
+// 0..39, so an id takes one 64-bit integer add per pair in L2 instead of a
+// count add and an fp64 add (the L2 atomic units take either add at about the
+// same rate).  Non-negative values in [B/256, B), B the power of two above the
+// largest value of the partition's first kPackedScaleSample values, are added
+// as round(v * 2^F) <= 2^25 (rounding error at most 2^-18 of the value); other
+// pairs take the count / fp64 adds.  If a sum field overflowed into its count
+// or a count wrapped, the decoded counts differ from the number of packed adds:
+// the finishing pass then sets kLargeRepair and guarded kernels redo the call
+// without packing.
+constexpr uint32_t kMaxPackedKeys = 1u << 22;
+// Smallest key space the automatic choice packs: below it a uniform key set
+// puts many adds on each packed word and the partitioned path is faster
+// (2^14 uniform keys: 0.67 against 0.51 ms; skewed keys prefer the direct
+// kernel at any size).
+constexpr uint32_t kMinPackedKeys = 1u << 17;
+constexpr uint32_t kPackedScaleSample = 65536;
+constexpr uint32_t kPackedCountShift = 40;
+constexpr uint32_t kLargeRepair = 8u;     // bit of *bad: redo the call without packing
+
+struct LargeFix {
+    float scale, inv;         // 2^F, 2^-F
+    uint32_t lo, span;        // value bit patterns packed: [lo, lo + span)
+    uint32_t on;              // 0: no window; every pair takes the count / fp64 adds
+    uint32_t pad;
+    unsigned long long npacked;   // pairs added to the packed words
+    unsigned long long ndecoded;  // counts decoded from them (finishing pass)
+};
 
 struct LargeKeyedArgs {
     const char* keys;
@@ -220,6 +254,10 @@ struct LargeKeyedArgs {
     scl_result* result;       // zeroed before the launch
     uint32_t* ticket;         // zero between launches (finishing pass)
     uint32_t* bad;            // zeroed before the launch
+    unsigned long long* packed;   // [num_keys] packed words, zeroed before; null: no packing
+    LargeFix* fix;            // the window (set by the scale pass) and its counters
+    uint32_t guard;           // 1: the kernel runs only if *bad has kLargeRepair
+    uint32_t pad;
 };
 
 // Device-polling server.  The host publishes jobs in pinned host memory that
@@ -311,6 +349,8 @@ extern int map_kernel_ipt();
 extern const void* tree_add_kernel_fn(int f32, int aligned, uint32_t k);
 extern const void* large_keyed_kernel_fn(int aligned);
 extern const void* large_keyed_finish_fn();
+extern const void* large_scale_fn();
+extern const void* large_repair_zero_fn();
 extern const void* doorbell_kernel_fn(int block, int ipt);
 
 }  // namespace scl

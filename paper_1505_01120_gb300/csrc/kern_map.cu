@@ -45,4 +45,8 @@ const void* large_keyed_kernel_fn(int aligned) {
 
 const void* large_keyed_finish_fn() { return (const void*)&dev::k_keyed_large_finish<256>; }
 
+const void* large_scale_fn() { return (const void*)&dev::k_large_scale<256>; }
+
+const void* large_repair_zero_fn() { return (const void*)&dev::k_large_repair_zero<256>; }
+
 }  // namespace scl

@@ -992,21 +992,85 @@ __global__ void __launch_bounds__(256) k_tree_add(const __grid_constant__ TreeAr
 
 // ------------------------------------------------- large key spaces
 
+// One pair of the direct path: ids below kMaxKeys to the CTA's shared table;
+// the others to their packed word (a non-negative value inside the window w)
+// or to the count / fp64 adds.
 __device__ __forceinline__ void large_add(uint32_t k, uint32_t vbits, const LargeKeyedArgs& a,
-                                          uint32_t* hc, float* hs, float* head, uint32_t& bad) {
+                                          const LargeFix& w, uint32_t* hc, float* hs,
+                                          float* head, uint32_t& bad, uint32_t& npk) {
     const float v = __uint_as_float(vbits);
     if (k >= a.num_keys) {
         bad = 1u;
     } else if (k < kMaxKeys) {
         atomicAdd(&hc[k], 1u);
         atomicAdd(k < kKeyedHead ? &head[k] : &hs[k], v);
+    } else if (w.on && vbits - w.lo < w.span) {   // a negative value's bits are never inside
+        atomicAdd(&a.packed[k], (1ull << kPackedCountShift) +
+                                    (unsigned long long)__float2uint_rn(v * w.scale));
+        ++npk;
     } else {
         atomicAdd(&a.counts[k], 1u);
         atomicAdd(&a.sums64[k], (double)v);
     }
 }
 
-// Grid-stride over pieces of kLargePiece pairs; each piece zeroes the shared
+// Whether a guarded kernel of the repair chain has nothing to do.
+__device__ __forceinline__ bool large_skip(const LargeKeyedArgs& a) {
+    return a.guard && !(__ldcg(a.bad) & kLargeRepair);
+}
+
+// The packed window of a partition (one CTA): B is the power of two above the
+// largest finite non-negative value among the first kPackedScaleSample
+// values, F = 25 - log2 B, packed values lie in [B/256, B).  No window (on =
+// 0) when that value is 0 or outside [2^-90, 2^90).
+template <int FB>
+__global__ void __launch_bounds__(FB) k_large_scale(const __grid_constant__ LargeKeyedArgs a) {
+    __shared__ uint32_t wm[FB / 32];
+    const uint64_t ns = min(a.n, (uint64_t)kPackedScaleSample);
+    uint32_t m = 0;
+    for (uint64_t i = threadIdx.x; i < ns; i += FB) {
+        const uint32_t b = ld_stream_b32(a.vals + i * 4);
+        if (b < 0x7f800000u) m = max(m, b);   // finite and not negative
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < FB / 32; ++q) m = max(m, wm[q]);
+        LargeFix f;
+        f.scale = f.inv = 0.f;
+        f.lo = f.span = 0u;
+        f.on = m >= 0x12800000u && m < 0x6c800000u;   // [2^-90, 2^90)
+        if (f.on) {
+            const int e1 = (int)(m >> 23) - 127 + 1;   // B = 2^e1
+            const int F = 25 - e1;
+            f.scale = __uint_as_float((uint32_t)(F + 127) << 23);
+            f.inv = __uint_as_float((uint32_t)(127 - F) << 23);
+            f.lo = (uint32_t)(e1 - 8 + 127) << 23;
+            f.span = ((uint32_t)(e1 + 127) << 23) - f.lo;
+        }
+        f.pad = 0u;
+        f.npacked = 0ull;
+        f.ndecoded = 0ull;
+        *a.fix = f;
+    }
+}
+
+// First kernel of the repair chain: the outputs and the result back to zero
+// (the guarded direct pass and finishing pass follow, without packing).
+template <int FB>
+__global__ void __launch_bounds__(FB) k_large_repair_zero(const __grid_constant__ LargeKeyedArgs a) {
+    if (large_skip(a)) return;
+    for (uint64_t k = (uint64_t)blockIdx.x * FB + threadIdx.x; k < a.num_keys;
+         k += (uint64_t)gridDim.x * FB) {
+        a.counts[k] = 0u;
+        a.sums64[k] = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(scl_result) / 4)
+        reinterpret_cast<uint32_t*>(a.result)[threadIdx.x] = 0u;
+}
+
+// Grid-stride over pieces of kDirectPiece pairs; each piece zeroes the shared
 // hot table (and the head copies of its first ids), accumulates, and flushes
 // its non-zero entries to global memory.
 template <bool ALIGNED>
@@ -1014,10 +1078,17 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
     __shared__ uint32_t hc[kMaxKeys];
     __shared__ float hs[kMaxKeys];
     __shared__ float heads[kKeyedHeadWords(256)];
+    if (large_skip(a)) return;
+    LargeFix w;
+    w.on = 0u;
+    w.lo = w.span = 0u;
+    w.scale = 0.f;
+    if (a.packed) w = *a.fix;
+    uint32_t npk = 0;
     float* head = heads + ((threadIdx.x >> 5) * kKeyedHeadClasses +
                            (threadIdx.x & (kKeyedHeadClasses - 1))) * kKeyedHeadStride;
     const uint32_t hot = min(a.num_keys, kMaxKeys);
-    const uint64_t npieces = (a.n + kLargePiece - 1) / kLargePiece;
+    const uint64_t npieces = (a.n + kDirectPiece - 1) / kDirectPiece;
     uint32_t bad = 0;
     for (uint64_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
         for (uint32_t i = threadIdx.x; i < hot; i += blockDim.x) {
@@ -1026,8 +1097,8 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
         }
         for (uint32_t i = threadIdx.x; i < kKeyedHeadWords(256); i += blockDim.x) heads[i] = 0.f;
         __syncthreads();
-        const uint64_t b = pc * kLargePiece;
-        const uint64_t e = min(b + kLargePiece, a.n);
+        const uint64_t b = pc * kDirectPiece;
+        const uint64_t e = min(b + kDirectPiece, a.n);
         uint64_t i = b;
         if constexpr (ALIGNED) {
             constexpr uint32_t CH = 256 * 4 * 4;
@@ -1040,16 +1111,16 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
                 for (int j = 0; j < 4; ++j) vv[j] = ld_stream_v4(a.vals + off + (size_t)j * 4096);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    large_add(kv[j].x, vv[j].x, a, hc, hs, head, bad);
-                    large_add(kv[j].y, vv[j].y, a, hc, hs, head, bad);
-                    large_add(kv[j].z, vv[j].z, a, hc, hs, head, bad);
-                    large_add(kv[j].w, vv[j].w, a, hc, hs, head, bad);
+                    large_add(kv[j].x, vv[j].x, a, w, hc, hs, head, bad, npk);
+                    large_add(kv[j].y, vv[j].y, a, w, hc, hs, head, bad, npk);
+                    large_add(kv[j].z, vv[j].z, a, w, hc, hs, head, bad, npk);
+                    large_add(kv[j].w, vv[j].w, a, w, hc, hs, head, bad, npk);
                 }
             }
         }
         for (uint64_t g = i + threadIdx.x; g < e; g += blockDim.x)
-            large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, hc, hs,
-                      head, bad);
+            large_add(ld_stream_b32(a.keys + g * 4), ld_stream_b32(a.vals + g * 4), a, w, hc, hs,
+                      head, bad, npk);
         __syncthreads();
         fold_head_copies(heads, hs, min(hot, kKeyedHead));
         __syncthreads();
@@ -1063,32 +1134,57 @@ __global__ void __launch_bounds__(256) k_keyed_large(const __grid_constant__ Lar
         __syncthreads();   // the table is zeroed again by the next piece
     }
     if (bad) atomicOr(a.bad, 1u);
+    if (a.packed) {
+        const uint32_t wn = __reduce_add_sync(0xffffffffu, npk);
+        if ((threadIdx.x & 31) == 0 && wn) atomicAdd(&a.fix->npacked, (unsigned long long)wn);
+    }
 }
 
-// Finishing pass: fp32 sums, totals (count exact, value sum fp64) and status.
-// The last CTA writes f32_sum and resets the ticket.
+// Finishing pass: the packed words decoded into the count / fp64 tables (if
+// any), fp32 sums, totals (count exact, value sum fp64) and status.  The last
+// CTA writes f32_sum, checks that the decoded counts add up to the packed adds
+// (else kLargeRepair: the guarded repair chain follows) and resets the ticket.
 template <int FB>
 __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant__ LargeKeyedArgs a) {
     static_assert(FB == 256, "finish block");
     __shared__ RedSmem sm;
-    unsigned long long c = 0;
+    if (large_skip(a)) return;
+    const double inv = a.packed ? (double)a.fix->inv : 0.0;
+    unsigned long long c = 0, cp = 0;
     ff s{0.f, 0.f};
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.num_keys;
          k += (uint64_t)gridDim.x * blockDim.x) {
-        const double v = a.sums64[k];
+        double v = a.sums64[k];
+        uint32_t ck = a.counts[k];
+        if (a.packed) {
+            const unsigned long long w = a.packed[k];
+            if (w) {
+                const uint32_t pc = (uint32_t)(w >> kPackedCountShift);
+                const unsigned long long q = w & ((1ull << kPackedCountShift) - 1);
+                cp += pc;
+                ck += pc;
+                v += (double)q * inv;
+                a.counts[k] = ck;
+                a.sums64[k] = v;
+            }
+        }
         a.sums32[k] = (float)v;
-        c += a.counts[k];
+        c += ck;
         s = ff_add(s, ff_of_double(v));
     }
     float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
     block_reduce_ff<256>(s, d0, d1, sm);
     c = block_sum_u64<256>(c, sm);
+    if (a.packed) cp = block_sum_u64<256>(cp, sm);
     if (threadIdx.x == 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&a.result->u64_sum), c);
         atomicAdd(&a.result->f64_sum, ff_to_double(s));
+        if (a.packed && cp) atomicAdd(&a.fix->ndecoded, cp);
         __threadfence();
         if (atomicAdd(a.ticket, 1u) == gridDim.x - 1) {
             __threadfence();
+            if (a.packed && __ldcg(&a.fix->ndecoded) != __ldcg(&a.fix->npacked))
+                atomicOr(a.bad, kLargeRepair);
             scl_result* r = a.result;
             const double tot = __ldcg(&r->f64_sum);
             r->f32_sum = (float)tot;
@@ -1097,7 +1193,7 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
             // bit 0: a key out of range; bit 1: the bucket-partitioned path
             // counted the keys differently in its two reads (they changed);
             // bit 2: one of its bounded waits ran out
-            const uint32_t bad = __ldcg(a.bad);
+            const uint32_t bad = __ldcg(a.bad) & 7u;
             r->status = (bad & 4u) ? SCL_E_TIMEOUT
                         : (bad & 2u) ? SCL_E_STATE : bad ? SCL_E_KEY_RANGE : SCL_OK;
             r->n = a.n;

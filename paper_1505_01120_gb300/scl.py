@@ -167,6 +167,7 @@ _SIGS = {
     "scl_load_partition_kv": ([_P, _P, _P, _u64, _P, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_wrap_device": ([_P, _P, _P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_alloc_partition": ([_P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
+    "scl_set_large_path": ([_P, ctypes.c_int], ctypes.c_int),
     "scl_free_partition": ([_P, _u64], ctypes.c_int),
     "scl_reload_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
     "scl_partition_info": ([_P, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
@@ -311,6 +312,14 @@ def scl_load_partition_kv(ctx: int, keys, vals, n: int | None = None, stream: in
     out = _u64()
     _check(lib.scl_load_partition_kv(ctx, _ptr(keys), _ptr(vals), n, stream, ctypes.byref(out)))
     return out.value
+
+
+SCL_LARGE_AUTO, SCL_LARGE_PACKED, SCL_LARGE_PARTITIONED, SCL_LARGE_DIRECT = 0, 1, 2, 3
+
+
+def scl_set_large_path(ctx: int, path: int) -> None:
+    """Path of this context's later large-key reduces (SCL_LARGE_*)."""
+    _check(lib.scl_set_large_path(ctx, path))
 
 
 def scl_alloc_partition(ctx: int, dtype: int, n: int) -> int:

@@ -48,3 +48,19 @@ def check_keyed(cnt, sums, s64, keys, vals, nk):
             float(np.max(np.abs(s64[nz] - osum[nz]) / np.abs(osum[nz])))
     assert np.all(np.abs(sums[nz].astype(np.float64) - osum[nz]) <= REL * np.abs(osum[nz]))
     return bad
+
+
+def check_keyed_nonfinite(cnt, sums, s64, keys, vals, nk):
+    """check_keyed where some sums are inf or NaN: those must match the
+    oracle's (NaN where it has NaN, the same infinity); the finite ones are
+    within the fp32 tolerance."""
+    ocnt, osum, _ = oracle.keyed_count_sum(keys, vals, nk)
+    assert np.array_equal(cnt, ocnt)
+    fin = np.isfinite(osum)
+    assert np.array_equal(np.isnan(s64), np.isnan(osum))
+    assert np.array_equal(np.isinf(s64), np.isinf(osum))
+    assert np.array_equal(np.sign(s64[np.isinf(osum)]), np.sign(osum[np.isinf(osum)]))
+    nz = fin & (ocnt > 0)
+    assert np.all(np.abs(s64[nz] - osum[nz]) <= REL * np.abs(osum[nz]))
+    assert np.all(np.abs(sums[nz].astype(np.float64) - osum[nz]) <= REL * np.abs(osum[nz]))
+

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import REL, check_keyed
+from gpu_common import REL, check_keyed, check_keyed_nonfinite
 
 pytestmark = pytest.mark.gpu
 
@@ -41,18 +41,6 @@ def _run(env, keys, vals, nk):
         scl.scl_free_partition(c.handle, p)
     assert r.status == 0 and r.u64_sum == keys.size
     return cnt, sums, s64
-
-
-def _check_nonfinite(cnt, sums, s64, keys, vals, nk):
-    ocnt, osum, _ = oracle.keyed_count_sum(keys, vals, nk)
-    assert np.array_equal(cnt, ocnt)
-    fin = np.isfinite(osum)
-    assert np.array_equal(np.isnan(s64), np.isnan(osum))
-    assert np.array_equal(np.isinf(s64), np.isinf(osum))
-    assert np.array_equal(np.sign(s64[np.isinf(osum)]), np.sign(osum[np.isinf(osum)]))
-    nz = fin & (ocnt > 0)
-    assert np.all(np.abs(s64[nz] - osum[nz]) <= REL * np.abs(osum[nz]))
-    assert np.all(np.abs(sums[nz].astype(np.float64) - osum[nz]) <= REL * np.abs(osum[nz]))
 
 
 @pytest.mark.parametrize("n", [16_384, 65_536 * 3 + 4097, 2_000_003])
@@ -102,7 +90,7 @@ def test_nan_and_inf(env):
     vals[5] = np.inf            # inside the first chunk
     keys[5] = 400
     cnt, sums, s64 = _run(env, keys, vals, 4096)
-    _check_nonfinite(cnt, sums, s64, keys, vals, 4096)
+    check_keyed_nonfinite(cnt, sums, s64, keys, vals, 4096)
 
 
 def test_window_overflow_reruns_on_the_fp32_table(env):

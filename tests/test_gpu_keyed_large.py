@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import check_keyed
+from gpu_common import check_keyed, check_keyed_nonfinite
 from paper_1505_01120_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -135,10 +135,24 @@ def _launches(scl, fn):
     return out, scl.scl_kernel_launches_total() - before
 
 
-# Bucket-partitioned path (partitions of at least 2^20 aligned pairs over more
-# than 4096 keys): histogram, scan, the two scatter forms (one of them returns
-# at once), the per-bucket reduce, then the finishing pass -- 6 launches; the
-# direct path makes 2.
+class _path:
+    """The context's large-key path for one test, back to automatic after."""
+
+    def __init__(self, scl, ctx, path):
+        self.scl, self.ctx, self.path = scl, ctx, path
+
+    def __enter__(self):
+        self.scl.scl_set_large_path(self.ctx, self.path)
+
+    def __exit__(self, *exc):
+        self.scl.scl_set_large_path(self.ctx, self.scl.SCL_LARGE_AUTO)
+
+
+# Bucket-partitioned path (chosen with SCL_LARGE_PARTITIONED; taken for
+# partitions of at least 2^20 aligned pairs over more than 4096 keys):
+# histogram, scan, the two scatter forms (one of them returns at once), the
+# per-bucket reduce, then the finishing pass -- 6 launches; the direct path
+# makes 2.
 RADIX_CASES = {
     # every pair on an id below 1024: counted in the scatter's hot tables, the
     # partition stays empty
@@ -193,8 +207,9 @@ def test_large_radix_cases(env, case):
     nk, keys = RADIX_CASES[case](rng)
     vals = rng.random(keys.size, dtype=np.float32)
     p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
-    (cnt, sums, s64, r), nl = _launches(
-        scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
+    with _path(scl, c.handle, scl.SCL_LARGE_PARTITIONED):
+        (cnt, sums, s64, r), nl = _launches(
+            scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
     assert nl == 6
     assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
     assert r.status == 0 and r.u64_sum == keys.size and r.n == keys.size
@@ -211,7 +226,7 @@ def test_large_radix_out_of_range(env):
     keys[[0, 1, 4096, n // 2, n - 1]] = [nk, -1, 1 << 30, nk + 4096, -(1 << 31)]
     vals = rng.random(n, dtype=np.float32)
     p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
-    with pytest.raises(scl.SclError) as e:
+    with _path(scl, c.handle, scl.SCL_LARGE_PARTITIONED), pytest.raises(scl.SclError) as e:
         scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st)
     assert e.value.status == scl.SCL_E_KEY_RANGE
     cnt, sums, s64, r = e.value.tables
@@ -235,10 +250,11 @@ def test_large_radix_and_direct_agree(env):
     whole = scl.scl_wrap_device(c.handle, dk.data_ptr(), dv.data_ptr(), scl.SCL_KV_I32_F32, n)
     tail = scl.scl_wrap_device(c.handle, dk.data_ptr() + 4, dv.data_ptr() + 4,
                                scl.SCL_KV_I32_F32, n - 1)
-    (a, _, _, _), na = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, whole, nk,
-                                                                        stream=st))
-    (b, bs, b64, _), nb_ = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, tail, nk,
+    with _path(scl, c.handle, scl.SCL_LARGE_PARTITIONED):
+        (a, _, _, _), na = _launches(scl, lambda: scl.scl_keyed_reduce_large(c.handle, whole, nk,
                                                                             stream=st))
+        (b, bs, b64, _), nb_ = _launches(scl, lambda: scl.scl_keyed_reduce_large(
+            c.handle, tail, nk, stream=st))
     assert (na, nb_) == (6, 2)
     ref = np.bincount(keys, minlength=nk).astype(np.uint32)
     assert np.array_equal(a, ref)
@@ -262,6 +278,7 @@ def test_large_radix_falls_back_when_arena_is_short():
     # partition 16 MiB + tables 4 MiB fit; another 16 MiB for the buckets does not
     with Context(24 << 20, device=0) as c:
         st = current_stream(0)
+        scl.scl_set_large_path(c.handle, scl.SCL_LARGE_PARTITIONED)
         p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
         (cnt, sums, s64, r), nl = _launches(
             scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
@@ -289,10 +306,137 @@ def test_large_async_buffer_grows_and_is_reused(env):
         p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
         torch.cuda.synchronize()
         before = scl.scl_kernel_launches_total()
-        scl.scl_keyed_reduce_large_async(c.handle, p, nk, dc, ds, d64, dr, stream=s2.cuda_stream)
+        with _path(scl, c.handle, scl.SCL_LARGE_PARTITIONED):
+            scl.scl_keyed_reduce_large_async(c.handle, p, nk, dc, ds, d64, dr,
+                                             stream=s2.cuda_stream)
         nl = scl.scl_kernel_launches_total() - before
         torch.cuda.synchronize()
         assert nl == 6
         assert check_keyed(dc.cpu().numpy().view(np.uint32), ds.cpu().numpy(),
                            d64.cpu().numpy(), keys, vals, nk) == 0
         scl.scl_free_partition(c.handle, p)
+
+
+# Packed direct path (the default for 2^17 to 2^22 keys): the scale pass, the direct
+# kernel with packed L2 words, the finishing pass, then the three guarded
+# kernels of the repair chain -- 6 launches whether or not the repair runs.
+
+def test_packed_values_on_both_sides_of_the_window(env):
+    """Values below the window, above it, negative, zeros, NaN and inf, on ids
+    above and below 4096: exact counts, sums within the fp32 tolerance,
+    non-finite sums as the oracle's."""
+    c, scl, st, _ = env
+    rng = np.random.default_rng(2400)
+    nk, n = 1 << 20, 3_000_017
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    vals = rng.random(n, dtype=np.float32)
+    idx = rng.choice(n, size=n // 40, replace=False)
+    q = len(idx) // 5
+    vals[idx[:q]] = rng.random(q, dtype=np.float32) * np.float32(1e-4)
+    vals[idx[q:2 * q]] = np.float32(2.0) + rng.random(q, dtype=np.float32) * 1000
+    vals[idx[2 * q:3 * q]] = 0.0
+    vals[idx[3 * q:4 * q]] = -0.0
+    vals[idx[4 * q:]] = -rng.random(len(idx) - 4 * q, dtype=np.float32) * np.float32(1e-3)
+    vals[[7, 1000, 2_000_000]] = [np.nan, np.inf, -np.inf]
+    keys[[7, 1000, 2_000_000]] = [5000, 100, 700_000]
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    (cnt, sums, s64, r), nl = _launches(
+        scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
+    assert nl == 6 and r.status == 0 and r.u64_sum == n
+    check_keyed_nonfinite(cnt, sums, s64, keys, vals, nk)
+    scl.scl_free_partition(c.handle, p)
+
+
+@pytest.mark.parametrize("hot", [40_000, 17_000_000])
+def test_packed_overflow_is_repaired(env, hot):
+    """One id far above 4096 takes more packed pairs than its word holds:
+    40,000 values near 1 overflow the 40-bit sum (limit 32,768 at 2^25 each);
+    17 M pairs also wrap the 24-bit count.  The finishing pass sees the
+    decoded counts fall short of the packed adds and the repair chain redoes
+    the call without packing: the same tables."""
+    c, scl, st, _ = env
+    rng = np.random.default_rng(2500 + hot % 97)
+    nk = 1 << 20
+    n = hot + 1_000_003
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    keys[rng.permutation(n)[:hot]] = 654_321
+    vals = (np.float32(0.5) + np.float32(0.5) * rng.random(n, dtype=np.float32)).astype(np.float32)
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    (cnt, sums, s64, r), nl = _launches(
+        scl, lambda: scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st))
+    assert nl == 6 and r.status == 0 and r.u64_sum == n
+    assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+    assert cnt[654_321] >= hot
+    scl.scl_free_partition(c.handle, p)
+
+
+@pytest.mark.parametrize("kind", ["negative", "zeros", "huge"])
+def test_packed_without_a_window(env, kind):
+    """No window (no non-negative finite value, only zeros, or values beyond
+    2^90): every pair takes the count / fp64 adds; same tables."""
+    c, scl, st, _ = env
+    rng = np.random.default_rng(2600)
+    nk, n = 100_000, 1_500_000
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    if kind == "negative":
+        vals = -rng.random(n, dtype=np.float32)
+    elif kind == "zeros":
+        vals = np.zeros(n, np.float32)
+    else:
+        vals = (rng.random(n, dtype=np.float32) * np.float32(1e30)).astype(np.float32)
+    p = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    with _path(scl, c.handle, scl.SCL_LARGE_PACKED):
+        cnt, sums, s64, r = scl.scl_keyed_reduce_large(c.handle, p, nk, stream=st)
+    assert r.status == 0 and r.u64_sum == n
+    if kind == "zeros":
+        ocnt, _, _ = oracle.keyed_count_sum(keys, vals, nk)
+        assert np.array_equal(cnt, ocnt) and np.all(s64 == 0) and np.all(sums == 0)
+    else:
+        assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+    scl.scl_free_partition(c.handle, p)
+
+
+def test_packed_unaligned_async_and_paths_agree(env):
+    """An unaligned view (the direct kernel's scalar loads) through the
+    packed path, twice in a row on device tables; the direct path without
+    packing and the partitioned path give the same counts and sums within
+    the tolerance; an unknown path is rejected."""
+    c, scl, st, torch = env
+    rng = np.random.default_rng(2700)
+    nk, n = 1 << 21, (1 << 21) + 3
+    keys = rng.integers(0, nk, size=n, dtype=np.int32)
+    vals = rng.random(n, dtype=np.float32)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    torch.cuda.synchronize()
+    tail = scl.scl_wrap_device(c.handle, dk.data_ptr() + 4, dv.data_ptr() + 4,
+                               scl.SCL_KV_I32_F32, n - 1)
+    whole = scl.scl_wrap_device(c.handle, dk.data_ptr(), dv.data_ptr(), scl.SCL_KV_I32_F32, n)
+    dc = torch.empty(nk, dtype=torch.int32, device="cuda")
+    ds = torch.empty(nk, dtype=torch.float32, device="cuda")
+    d64 = torch.empty(nk, dtype=torch.float64, device="cuda")
+    dr = torch.empty(48, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        scl.scl_keyed_reduce_large_async(c.handle, tail, nk, dc, ds, d64, dr, stream=st)
+        torch.cuda.synchronize()
+        assert check_keyed(dc.cpu().numpy().view(np.uint32), ds.cpu().numpy(),
+                           d64.cpu().numpy(), keys[1:], vals[1:], nk) == 0
+        res = dr.cpu().numpy().view(scl.RESULT_DTYPE)[0]
+        assert int(res["status"]) == 0 and int(res["u64_sum"]) == n - 1
+    tables = {}
+    for path, want in ((scl.SCL_LARGE_PACKED, 6), (scl.SCL_LARGE_DIRECT, 2),
+                       (scl.SCL_LARGE_PARTITIONED, 6)):
+        with _path(scl, c.handle, path):
+            (cnt, sums, s64, r), nl = _launches(
+                scl, lambda: scl.scl_keyed_reduce_large(c.handle, whole, nk, stream=st))
+        assert nl == want
+        assert check_keyed(cnt, sums, s64, keys, vals, nk) == 0
+        tables[path] = cnt
+    assert np.array_equal(tables[scl.SCL_LARGE_PACKED], tables[scl.SCL_LARGE_DIRECT])
+    assert np.array_equal(tables[scl.SCL_LARGE_PACKED], tables[scl.SCL_LARGE_PARTITIONED])
+    with pytest.raises(scl.SclError) as e:
+        scl.scl_set_large_path(c.handle, 9)
+    assert e.value.status == scl.SCL_E_INVALID
+    scl.scl_free_partition(c.handle, tail)
+    scl.scl_free_partition(c.handle, whole)
+
