@@ -70,7 +70,9 @@ constexpr uint32_t kKeyedFastSmemBytes = kFixMaxOffset + 16 * 4;
 constexpr uint64_t kKeyedPieceAlign = 64;           // piece boundaries, in pairs
 constexpr uint64_t kKeyedMinPiece = 32768;          // pairs; keeps table flushes cheap
 constexpr uint64_t kKeyedMinFragment = 8192;        // pairs; shorter end pieces join a neighbour
-constexpr uint64_t kKeyedTaskOverhead = 4096;       // pair-equivalents per keyed task
+constexpr uint64_t kKeyedTaskOverhead = 4096;       // pair-equivalents per keyed task (default)
+constexpr uint64_t kKeyedPieceOverheadFast = 32;    // per thread of a keyed-only CTA
+constexpr uint64_t kKeyedPieceOverheadMixed = 16;   // per thread of a mixed-kernel CTA
 constexpr uint32_t kMaxSegChunks = 4;               // a streaming segment is 1..4 chunks
 constexpr uint32_t kTargetSegsPerTask = 256;
 constexpr uint32_t kFoldBlock = 256;                // keyed fold kernel block size

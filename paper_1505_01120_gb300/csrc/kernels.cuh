@@ -43,6 +43,12 @@ __device__ __forceinline__ uint32_t ld_stream_b32(const void* p) {
     return v;
 }
 
+// Asks L2 for the 128-byte line holding p (no register result, no fault
+// semantics beyond those of a load of p; p must lie inside an allocation).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void st_stream_v4(void* p, uint4 v) {
     asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};"
                  :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
@@ -183,6 +189,33 @@ __device__ __forceinline__ void block_reduce_ff(ff& s, float& mn, float& mx, Red
         s = ff_add(s, ff_shfl_xor(s, o));
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __syncthreads();
+}
+
+// block_reduce_ff of a sum and block_sum_u64 of a count in one exchange (same
+// association orders, so the same totals), for the keyed write-out.
+template <int BLOCK>
+__device__ __forceinline__ void block_reduce_ff_u64(ff& s, unsigned long long& u, RedSmem& sm) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s = ff_add(s, ff_shfl_xor(s, o));
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sm.shi[w] = s.hi;
+        sm.slo[w] = s.lo;
+        sm.u[w] = u;
+    }
+    __syncthreads();
+    const bool in = l < BLOCK / 32;
+    s = in ? ff{sm.shi[l], sm.slo[l]} : ff{0.f, 0.f};
+    u = in ? sm.u[l] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s = ff_add(s, ff_shfl_xor(s, o));
+        u += __shfl_xor_sync(0xffffffffu, u, o);
     }
     __syncthreads();
 }
@@ -430,8 +463,26 @@ __device__ __forceinline__ uint32_t fix_fold(uint32_t nk, const uint32_t* cnt, f
     return over;
 }
 
+// Asks L2 for pairs [c, min(c + BLOCK*IPT*4, e)) of a key array and a value
+// array: one prefetch per 128 bytes, spread over the CTA, every address
+// inside the range.
+template <int BLOCK, int IPT>
+__device__ __forceinline__ void prefetch_chunk_l2(const char* kb, const char* vb, uint64_t c,
+                                                  uint64_t e) {
+    constexpr uint64_t CH = (uint64_t)BLOCK * IPT * 4;
+    const uint64_t len = c < e ? min(e - c, CH) : 0ull;
+    const uint32_t lines = (uint32_t)((len + 31) / 32);   // 32 pairs = 128 bytes per array
+    for (uint32_t l = threadIdx.x; l < 2 * lines; l += BLOCK) {
+        const bool key = l < lines;
+        const uint64_t el = c + (uint64_t)(key ? l : l - lines) * 32;   // < c + len <= e
+        prefetch_l2((key ? kb : vb) + el * 4);
+    }
+}
+
 // One pass over pairs [b, e): 128-bit loads of IPT vectors of keys and of
-// values per thread, then the table adds.  FIX: through the fixed-point
+// values per thread, then the table adds; while a chunk's adds run, the next
+// chunk is on its way into L2, so a warp's next loads wait on L2 rather than
+// DRAM.  FIX: through the fixed-point
 // window, folded every kFixWindow pairs and at the end; returns nonzero in
 // every thread if a window overflowed.
 template <int BLOCK, int IPT, bool HASHED, bool FIX>
@@ -473,6 +524,7 @@ __device__ __forceinline__ uint32_t keyed_pass(const DevTask& t, uint64_t b, uin
             for (int j = 0; j < IPT; ++j) kv[j] = ld_stream_v4(kb + off + (size_t)j * BLOCK * 16);
 #pragma unroll
             for (int j = 0; j < IPT; ++j) vv[j] = ld_stream_v4(vb + off + (size_t)j * BLOCK * 16);
+            prefetch_chunk_l2<BLOCK, IPT>(kb, vb, i + CH, e);
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 add(kv[j].x, vv[j].x);
@@ -481,6 +533,37 @@ __device__ __forceinline__ uint32_t keyed_pass(const DevTask& t, uint64_t b, uin
                 add(kv[j].w, vv[j].w);
             }
         }
+    }
+    // The last, partial chunk of aligned arrays: its whole vectors by 128-bit
+    // loads issued together (a thread past the end re-reads the chunk's first
+    // vector and drops it), then the at most 3 pairs after the last whole
+    // vector.  (i is a multiple of 4: pieces start at multiples of 64 pairs.)
+    if ((t.flags & TF_ALIGNED) && i < e) {
+        window(i);
+        const uint64_t ev = e & ~(uint64_t)3;
+        if (i + 4 <= ev) {
+            uint4 kv[IPT], vv[IPT];
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const uint64_t g = i + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
+                const uint64_t gc = g + 4 <= ev ? g : i;
+                kv[j] = ld_stream_v4(kb + gc * 4);
+                vv[j] = ld_stream_v4(vb + gc * 4);
+            }
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const uint64_t g = i + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
+                if (g + 4 <= ev) {
+                    add(kv[j].x, vv[j].x);
+                    add(kv[j].y, vv[j].y);
+                    add(kv[j].z, vv[j].z);
+                    add(kv[j].w, vv[j].w);
+                }
+            }
+        }
+        if (threadIdx.x < e - ev)
+            add(ld_stream_b32(kb + (ev + threadIdx.x) * 4), ld_stream_b32(vb + (ev + threadIdx.x) * 4));
+        i = e;
     }
     for (; i < e; i += CH) {
         window(i);
@@ -524,10 +607,32 @@ __device__ __forceinline__ void keyed_zero(uint32_t* tab, uint32_t nk) {
 
 // Largest finite |v| (as a bit pattern) over this thread's pairs of the first
 // chunk of [b, e); the chunk's values are read again from L2 by the pass.
+// Aligned arrays and a whole first chunk (every FAST piece: it holds at least
+// kFixMinPairs >= BLOCK*IPT*4 pairs) take IPT unconditional 128-bit loads,
+// all in flight at once; otherwise one guarded 32-bit load per pair.
+__device__ __forceinline__ uint32_t finite_abs_max4(uint32_t m, uint4 v) {
+    const uint32_t a[4] = {v.x & 0x7fffffffu, v.y & 0x7fffffffu, v.z & 0x7fffffffu,
+                           v.w & 0x7fffffffu};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (a[q] < 0x7f800000u) m = max(m, a[q]);
+    return m;
+}
+
 template <int BLOCK, int IPT>
 __device__ __forceinline__ uint32_t first_chunk_max(const DevTask& t, uint64_t b, uint64_t e) {
     const char* vb = static_cast<const char*>(t.in1);
     uint32_t m = 0;
+    constexpr uint64_t CH = (uint64_t)BLOCK * IPT * 4;
+    if ((t.flags & TF_ALIGNED) && e - b >= CH) {
+        uint4 v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j)
+            v[j] = ld_stream_v4(vb + (b + ((uint64_t)j * BLOCK + threadIdx.x) * 4) * 4);
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) m = finite_abs_max4(m, v[j]);
+        return m;
+    }
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const uint64_t g = b + ((uint64_t)j * BLOCK + threadIdx.x) * 4;
@@ -654,9 +759,7 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
             ctot += c;
             stot = ff_add_f(stot, s);
         }
-        float dummy0 = CUDART_INF_F, dummy1 = -CUDART_INF_F;
-        block_reduce_ff<BLOCK>(stot, dummy0, dummy1, sm);
-        ctot = block_sum_u64<BLOCK>(ctot, sm);
+        block_reduce_ff_u64<BLOCK>(stot, ctot, sm);
         if (threadIdx.x == 0) {
             write_result(t.result, ctot, ff_to_double(stot), CUDART_INF_F, -CUDART_INF_F,
                          any_bad ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
@@ -727,9 +830,11 @@ __global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT
                 const KPiece kp = a.kpieces[p];
                 const DevTask t = a.tasks[kp.task];
                 if (t.kind == K_KEYED_MIX)
-                    keyed_piece<BLOCK, KIPT, true, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, true, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end,
+                                                         tab, sm);
                 else
-                    keyed_piece<BLOCK, KIPT, false, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end, tab, sm);
+                    keyed_piece<BLOCK, KIPT, false, FAST>(a, t, kp.task, kp.slot, kp.begin, kp.end,
+                                                          tab, sm);
             }
         }
     }
@@ -834,9 +939,7 @@ __global__ void __launch_bounds__(FB) k_keyed_fold(const __grid_constant__ Kerne
         ctot = c;
         stot = s;
     }
-    float d0 = CUDART_INF_F, d1 = -CUDART_INF_F;
-    block_reduce_ff<kFoldBlock>(stot, d0, d1, sm);
-    ctot = block_sum_u64<kFoldBlock>(ctot, sm);
+    block_reduce_ff_u64<kFoldBlock>(stot, ctot, sm);
     if (threadIdx.x == 0) {
         StreamPartial* fp = a.fpart + (size_t)fi * (kMaxKeys / kFoldBlock) + blockIdx.x;
         fp->shi = stot.hi;

@@ -22,7 +22,7 @@ struct KeyedPlanPiece {
 
 // Keyed work of a batch over Gk CTAs (Gk >= 1).  `keyed` lists the keyed
 // tasks in batch order as (task index, pairs).  Each task costs
-// pairs + kKeyedTaskOverhead; CTA c takes the even share [W*c/Gk, W*(c+1)/Gk)
+// pairs + overhead; CTA c takes the even share [W*c/Gk, W*(c+1)/Gk)
 // of the total W, so a task is cut where the shares meet, at multiples of
 // kKeyedPieceAlign pairs.  A task of at most kKeyedMinPiece pairs stays whole,
 // on the CTA holding most of it; in a larger task, end pieces shorter than
@@ -30,10 +30,11 @@ struct KeyedPlanPiece {
 // (possibly empty) piece; pieces come out in task order with non-decreasing
 // CTAs, and together cover each task's [0, pairs) exactly once.
 inline void plan_keyed_pieces(const std::vector<std::pair<uint32_t, uint64_t>>& keyed,
-                              uint32_t Gk, std::vector<KeyedPlanPiece>* out) {
+                              uint32_t Gk, std::vector<KeyedPlanPiece>* out,
+                              uint64_t overhead = kKeyedTaskOverhead) {
     out->clear();
     uint64_t W = 0;
-    for (const auto& k : keyed) W += k.second + kKeyedTaskOverhead;
+    for (const auto& k : keyed) W += k.second + overhead;
     if (keyed.empty() || Gk == 0) return;
     auto R = [&](uint64_t cta) -> uint64_t { return (uint64_t)((unsigned __int128)cta * W / Gk); };
     struct Frag {
@@ -43,7 +44,7 @@ inline void plan_keyed_pieces(const std::vector<std::pair<uint32_t, uint64_t>>& 
     std::vector<Frag> frag;
     uint64_t A = 0;
     for (const auto& k : keyed) {
-        const uint64_t n = k.second, cost = n + kKeyedTaskOverhead, B = A + cost;
+        const uint64_t n = k.second, cost = n + overhead, B = A + cost;
         uint32_t c0 = (uint32_t)((unsigned __int128)A * Gk / W);
         while (c0 + 1 < Gk && R(c0 + 1) <= A) ++c0;
         while (c0 > 0 && R(c0) > A) --c0;

@@ -372,6 +372,16 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
 
 // ----------------------------------------------------------------- planner
 
+// The fixed cost of a keyed piece in pair-equivalents: zeroing the table,
+// the window scan, the first loads, the end-of-piece barriers and the
+// write-out, at the rate a CTA adds pairs.  Measured on the 10,000-task
+// batch's 3,374 keyed tasks (log-normal lengths, median 16 Ki pairs): the
+// keyed-only kernel (fixed-point window) balances best at 32 pairs per
+// thread of the CTA, the mixed kernel (fp32 table) at 16.
+static uint64_t keyed_piece_overhead(int mask, const Shape& s) {
+    return (uint64_t)s.block * (mask == M_KEYED ? kKeyedPieceOverheadFast : kKeyedPieceOverheadMixed);
+}
+
 int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     P->tasks.assign(nt, DevTask{});
     bool has_u32 = false, has_f32 = false, has_keyed = false;
@@ -411,10 +421,11 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     P->nseg_stream = 0;
     P->sslots = 0;
     uint64_t W = 0;   // keyed cost
+    const uint64_t kov = keyed_piece_overhead(P->mask, P->shape);
     for (uint32_t i = 0; i < nt; ++i) {
         DevTask& t = P->tasks[i];
         if (is_keyed(kind[i])) {
-            W += t.n + kKeyedTaskOverhead;
+            W += t.n + kov;
             continue;
         }
         t.seg_elems = stream_seg_elems(t.n, chunk);
@@ -458,7 +469,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
         for (uint32_t i = 0; i < nt; ++i)
             if (is_keyed(kind[i])) keyed.emplace_back(i, P->tasks[i].n);
         std::vector<KeyedPlanPiece> pieces;
-        plan_keyed_pieces(keyed, Gk, &pieces);
+        plan_keyed_pieces(keyed, Gk, &pieces, kov);
         for (size_t k = 0; k < pieces.size();) {
             const uint32_t i = pieces[k].task;
             size_t e = k;
