@@ -941,6 +941,15 @@ def batch_config(torch, scl, ctx, stream) -> dict:
     scl.scl_batch_capture(b, st)
     ms_batch = time_device(torch, stream, lambda: scl.scl_batch_launch(b, st), 10)
     res_batch = scl.scl_batch_results(b, n, stream=st)
+    kernels = scl.scl_batch_kernel_launches(b)
+    # the same batch as one launch of the mixed kernel
+    scl.scl_set_batch_split(ctx.handle, False)
+    bm = scl.scl_batch_create(ctx.handle, arr, n)
+    scl.scl_set_batch_split(ctx.handle, True)
+    scl.scl_batch_capture(bm, st)
+    ms_mixed = time_device(torch, stream, lambda: scl.scl_batch_launch(bm, st), 10)
+    res_mixed = scl.scl_batch_results(bm, n, stream=st)
+    scl.scl_batch_destroy(bm)
 
     dres = torch.zeros(n * 48, dtype=torch.uint8, device="cuda")
     dptr = dres.data_ptr()
@@ -959,6 +968,9 @@ def batch_config(torch, scl, ctx, stream) -> dict:
     same_int = bool(np.array_equal(res_each["u64_sum"], res_batch["u64_sum"]))
     f32 = np.array([s.kind == synth.KIND_POLY3 for s in specs])
     same_f32 = bool(np.array_equal(res_each["f64_sum"][f32], res_batch["f64_sum"][f32]))
+    keyed = np.array([s.kind == synth.KIND_KEYED for s in specs])
+    same_mixed = bool(np.array_equal(res_mixed[~keyed], res_batch[~keyed]) and
+                      np.array_equal(res_mixed["u64_sum"], res_batch["u64_sum"]))
 
     # the same per-partition launches captured once into a CUDA graph
     g = torch.cuda.CUDAGraph()
@@ -971,6 +983,13 @@ def batch_config(torch, scl, ctx, stream) -> dict:
     return {"tasks": n, "algorithmic_bytes": nbytes,
             "batched_graph_ms": ms_batch, "batched_tasks_per_s": n / ms_batch * 1e3,
             "batched_gbs": nbytes / ms_batch / 1e6,
+            "batched_frac_of_hbm": nbytes / ms_batch / 1e6 / peaks()["hbm_gbs"],
+            "batched_launch": "one persistent kernel per family (keyed, uint32, fp32), "
+                              "concurrent on forked streams, in one CUDA graph; %d kernels"
+                              % kernels,
+            "mixed_kernel_graph_ms": ms_mixed,
+            "mixed_kernel_frac_of_hbm": nbytes / ms_mixed / 1e6 / peaks()["hbm_gbs"],
+            "mixed_kernel_equals_split_streaming": same_mixed,
             "per_launch_ms": ms_each, "per_launch_tasks_per_s": n / ms_each * 1e3,
             "per_launch_graph_ms": ms_graph_each,
             "speedup_vs_per_launch": ms_each / ms_batch,

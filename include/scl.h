@@ -482,8 +482,15 @@ int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
  * partitions; the paper's "enough data" concern, Sec. 3 item 2, and kernel
  * caching per worker, Sec. 3.1.1.2).  Streaming tasks are cut into segments
  * that CTAs pull from a queue; keyed tasks into even shares of the keyed work
- * on a cost-weighted share of the CTAs (the rest stream meanwhile).  The
- * plan, task table and scratch are placed in the arena; nothing runs yet.
+ * (pairs plus a fixed cost per piece) over the CTAs that take keyed pieces.
+ * A batch whose tasks mix families (uint32, fp32, keyed) launches, with
+ * splitting on (the default, scl_set_batch_split), one persistent kernel per
+ * family, concurrently: the keyed-only kernel first on `stream`, the others
+ * on two side streams the batch owns, forked from `stream` and joined back
+ * into it.  With splitting off it is one launch of the mixed kernel, a
+ * cost-weighted share of whose CTAs take the keyed pieces while the rest
+ * stream.  The plan, task table and scratch are placed in the arena; nothing
+ * runs yet.
  * Tasks keep referencing their partitions: those must stay alive while the
  * batch exists.  Errors: SCL_E_INVALID, SCL_E_UNSUPPORTED, SCL_E_NOMEM. */
 int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks,
@@ -504,6 +511,13 @@ int scl_batch_capture(scl_batch* batch, void* stream);
  * SCL_E_TIMEOUT / SCL_E_STATE if the launch set its device error word (the
  * batch's scratch is then reset, so the next launch starts clean). */
 int scl_batch_results(scl_batch* batch, void* stream, scl_result* results);
+
+/* Whether later scl_batch_create calls of this context split a batch that
+ * mixes families into concurrent per-family launches (on = 1, the default;
+ * off = 0: one mixed-kernel launch).  Results are the same either way except
+ * the fp32 keyed sums, which are rounded in a different order.
+ * Errors: SCL_E_INVALID (on not 0 or 1). */
+int scl_set_batch_split(scl_ctx* ctx, int on);
 
 /* Kernel launches that one launch of this batch makes (for accounting). */
 int scl_batch_kernel_launches(scl_batch* batch, uint32_t* count);

@@ -43,16 +43,73 @@ double pairwise_sum(const scl_result* r, uint32_t lo, uint32_t hi) {
 
 }  // namespace
 
+// A batch is one launch group or, when its tasks mix families and splitting is
+// on, one group per family (keyed, uint32, fp32) launched concurrently on forked
+// streams: the keyed-only kernel (fixed-point window, two 512-thread CTAs per
+// SM) next to the streaming kernels (eight CTAs per SM), in place of the mixed
+// kernel whose CTAs hold the fp32 keyed table at four per SM.  Every group
+// writes into one scratch block: results, tickets and flags at the positions
+// of `order`, a header per group.
 struct scl_batch {
+    struct Group {
+        Plan plan;
+        PlanImage img;
+        KernelArgs args;
+        uint32_t first = 0, count = 0;   // positions [first, first + count) of `order`
+    };
     Ctx* ctx = nullptr;
-    Plan plan;
-    PlanImage img;
-    KernelArgs args;
+    std::vector<Group> groups;
+    std::vector<uint32_t> order;          // position -> the caller's task index
+    void* scratch = nullptr;              // results, tickets, flags, headers (zeroed)
+    size_t scratch_bytes = 0;
+    scl_result* results = nullptr;        // in `order`
+    uint32_t* hdr = nullptr;              // H_WORDS per group
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[2] = {nullptr, nullptr};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t ntasks = 0;
-    std::vector<scl_result> host_results;
+    uint32_t kernels = 0;                 // kernel launches per scl_batch_launch
+    std::vector<scl_result> staged;
 };
+
+namespace {
+
+// Frees what a batch holds on the device (after a device synchronisation).
+void batch_release(scl_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto& g : b->groups)
+        if (g.img.block) b->ctx->arena.release(g.img.block);
+    if (b->scratch) b->ctx->arena.release(b->scratch);
+    for (int i = 0; i < 2; ++i) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+}
+
+// The groups' launches on `st`: the first group on `st` itself, the others on
+// the batch's side streams, forked from `st` before and joined into it after.
+// Stream capture records the same fork and join.
+int batch_launch_groups(scl_batch* b, cudaStream_t st) {
+    if (b->groups.size() == 1) return launch_plan(b->ctx, b->groups[0].plan, b->groups[0].args, st);
+    SCL_CUDA(cudaEventRecord(b->fork, st));
+    for (size_t g = 1; g < b->groups.size(); ++g)
+        SCL_CUDA(cudaStreamWaitEvent(b->side[g - 1], b->fork, 0));
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        const scl_batch::Group& G = b->groups[g];
+        SCL_TRY(launch_plan(b->ctx, G.plan, G.args, g ? b->side[g - 1] : st));
+    }
+    for (size_t g = 1; g < b->groups.size(); ++g) {
+        SCL_CUDA(cudaEventRecord(b->join[g - 1], b->side[g - 1]));
+        SCL_CUDA(cudaStreamWaitEvent(st, b->join[g - 1], 0));
+    }
+    return SCL_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -939,22 +996,83 @@ int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks, scl_b
     if (!b) return fail(SCL_E_NOMEM, "host allocation failed");
     b->ctx = ctx;
     b->ntasks = ntasks;
-    int st = plan_tasks(ctx, tasks, ntasks, &b->plan);
-    std::vector<char> host;
-    if (st == SCL_OK && ntasks) st = build_image(ctx, b->plan, &b->img, &host, &b->args);
-    if (st == SCL_OK && ntasks) {
-        if (cudaMemcpy(b->img.block, host.data(), b->img.plan_bytes, cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
-            cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes) != cudaSuccess ||
-            cudaDeviceSynchronize() != cudaSuccess)   // order before launches on any stream
-            st = fail(SCL_E_CUDA, "uploading the batch plan failed");
-    }
-    if (st != SCL_OK) {
-        if (b->img.block) ctx->arena.release(b->img.block);
+    int st = SCL_OK;
+    auto bail = [&](int code) {
+        cudaDeviceSynchronize();
+        batch_release(b);
         delete b;
-        return st;
+        return code;
+    };
+    if (ntasks == 0) {
+        *out = b;
+        return SCL_OK;
     }
-    b->host_results.resize(ntasks);
+    // One plan over every task validates them and resolves their kinds.
+    Plan all;
+    st = plan_tasks(ctx, tasks, ntasks, &all);
+    if (st != SCL_OK) return bail(st);
+    std::vector<std::vector<uint32_t>> fam;
+    if (ctx->batch_split && all.mask == M_ALL) {
+        fam.resize(3);   // launch order: keyed (the longest), uint32, fp32
+        for (uint32_t i = 0; i < ntasks; ++i) {
+            const int m = mask_of_kind(all.tasks[i].kind);
+            fam[m == M_KEYED ? 0 : m == M_U32 ? 1 : 2].push_back(i);
+        }
+        fam.erase(std::remove_if(fam.begin(), fam.end(),
+                                 [](const std::vector<uint32_t>& v) { return v.empty(); }),
+                  fam.end());
+    } else {
+        fam.emplace_back(ntasks);
+        for (uint32_t i = 0; i < ntasks; ++i) fam[0][i] = i;
+    }
+    const size_t ng = fam.size();
+    const size_t o_tk = align_up(ntasks * sizeof(scl_result));
+    const size_t o_fl = o_tk + align_up(ntasks * 4ull);
+    const size_t o_hdr = o_fl + align_up(ntasks * 4ull);
+    b->scratch_bytes = o_hdr + ng * align_up(H_WORDS * 4);
+    b->scratch = ctx->arena.alloc(b->scratch_bytes);
+    if (!b->scratch)
+        return bail(fail(SCL_E_NOMEM, "arena: no block of %zu bytes for the batch", b->scratch_bytes));
+    char* z = static_cast<char*>(b->scratch);
+    b->results = reinterpret_cast<scl_result*>(z);
+    b->hdr = reinterpret_cast<uint32_t*>(z + o_hdr);
+    if (cudaMemset(z, 0, b->scratch_bytes) != cudaSuccess)
+        return bail(fail(SCL_E_CUDA, "zeroing the batch scratch failed"));
+    std::vector<scl_task> sub;
+    for (size_t g = 0; g < ng; ++g) {
+        scl_batch::Group& G = b->groups.emplace_back();
+        G.first = (uint32_t)b->order.size();
+        G.count = (uint32_t)fam[g].size();
+        sub.clear();
+        for (uint32_t i : fam[g]) {
+            b->order.push_back(i);
+            sub.push_back(tasks[i]);
+        }
+        st = plan_tasks(ctx, sub.data(), G.count, &G.plan);
+        if (st != SCL_OK) return bail(st);
+        ExternalScratch ext;
+        ext.results = b->results + G.first;
+        ext.tickets = reinterpret_cast<uint32_t*>(z + o_tk) + G.first;
+        ext.flags = reinterpret_cast<uint32_t*>(z + o_fl) + G.first;
+        ext.hdr = b->hdr + g * (align_up(H_WORDS * 4) / 4);
+        ext.task_cap = G.count;
+        std::vector<char> host;
+        st = build_image(ctx, G.plan, &G.img, &host, &G.args, &ext);
+        if (st != SCL_OK) return bail(st);
+        if (cudaMemcpy(G.img.block, host.data(), G.img.plan_bytes, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(fail(SCL_E_CUDA, "uploading the batch plan failed"));
+        b->kernels += 1u + (G.plan.fold_tasks.empty() ? 0u : 1u);
+    }
+    for (size_t g = 1; g < ng; ++g)
+        if (cudaStreamCreateWithFlags(&b->side[g - 1], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[g - 1], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(SCL_E_CUDA, "creating the batch's side streams failed"));
+    if (ng > 1 && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(SCL_E_CUDA, "creating the batch's fork event failed"));
+    if (cudaDeviceSynchronize() != cudaSuccess)   // order before launches on any stream
+        return bail(fail(SCL_E_CUDA, "uploading the batch plan failed"));
+    b->staged.resize(ntasks);
     *out = b;
     return SCL_OK;
 }
@@ -964,19 +1082,20 @@ int scl_batch_launch(scl_batch* b, void* stream) {
     CTX_ENTER(b->ctx);
     if (b->exec) {
         SCL_CUDA(cudaGraphLaunch(b->exec, S(stream)));
-        count_launches(1 + (b->plan.fold_tasks.empty() ? 0 : 1));
+        count_launches(b->kernels);
         return SCL_OK;
     }
-    return launch_plan(b->ctx, b->plan, b->args, S(stream));
+    if (b->groups.empty()) return SCL_OK;
+    return batch_launch_groups(b, S(stream));
 }
 
 int scl_batch_capture(scl_batch* b, void* stream) {
     if (!b) return fail(SCL_E_INVALID, "null batch");
     CTX_ENTER(b->ctx);
-    if (b->exec) return SCL_OK;
+    if (b->exec || b->groups.empty()) return SCL_OK;
     SCL_CUDA(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
     const uint64_t before = launches_total();
-    int st = launch_plan(b->ctx, b->plan, b->args, S(stream));
+    int st = batch_launch_groups(b, S(stream));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(S(stream), &g);
     count_launches(0 - (launches_total() - before));   // capture launched nothing
@@ -1000,29 +1119,38 @@ int scl_batch_results(scl_batch* b, void* stream, scl_result* results) {
     if (!b) return fail(SCL_E_INVALID, "null batch");
     CTX_ENTER(b->ctx);
     if (b->ntasks && !results) return fail(SCL_E_INVALID, "null results");
-    uint32_t err = 0;
-    if (b->ntasks) {
-        SCL_CUDA(cudaMemcpyAsync(results, b->img.results, b->ntasks * sizeof(scl_result),
-                                 cudaMemcpyDeviceToHost, S(stream)));
-        SCL_CUDA(cudaMemcpyAsync(&err, b->img.hdr + H_ERROR, 4, cudaMemcpyDeviceToHost,
-                                 S(stream)));
-    }
+    if (!b->ntasks) return SCL_OK;
+    const size_t hw = align_up(H_WORDS * 4) / 4;
+    std::vector<uint32_t> hdr(b->groups.size() * hw);
+    SCL_CUDA(cudaMemcpyAsync(b->staged.data(), b->results, b->ntasks * sizeof(scl_result),
+                             cudaMemcpyDeviceToHost, S(stream)));
+    SCL_CUDA(cudaMemcpyAsync(hdr.data(), b->hdr, hdr.size() * 4, cudaMemcpyDeviceToHost, S(stream)));
     SCL_CUDA(cudaStreamSynchronize(S(stream)));
+    uint32_t err = 0;
+    for (size_t g = 0; g < b->groups.size(); ++g) err |= hdr[g * hw + H_ERROR];
     if (err) {
-        SCL_CUDA(cudaMemset((char*)b->img.block + b->img.zero_off, 0, b->img.zero_bytes));
+        SCL_CUDA(cudaMemset(b->scratch, 0, b->scratch_bytes));
         SCL_CUDA(cudaDeviceSynchronize());
         return fail((err & 4u) ? SCL_E_TIMEOUT : SCL_E_STATE,
                     "device error word 0x%x after the batch", err);
     }
+    for (uint32_t p = 0; p < b->ntasks; ++p) results[b->order[p]] = b->staged[p];
     for (uint32_t i = 0; i < b->ntasks; ++i)
         if (results[i].status == SCL_E_KEY_RANGE)
             return fail(SCL_E_KEY_RANGE, "task %u saw a key out of range", i);
     return SCL_OK;
 }
 
+int scl_set_batch_split(scl_ctx* ctx, int on) {
+    CTX_ENTER(ctx);
+    if (on != 0 && on != 1) return fail(SCL_E_INVALID, "batch split must be 0 or 1, not %d", on);
+    ctx->batch_split = on;
+    return SCL_OK;
+}
+
 int scl_batch_kernel_launches(scl_batch* b, uint32_t* count) {
     if (!b || !count) return fail(SCL_E_INVALID, "null argument");
-    *count = b->ntasks ? 1u + (b->plan.fold_tasks.empty() ? 0u : 1u) : 0u;
+    *count = b->kernels;
     return SCL_OK;
 }
 
@@ -1032,9 +1160,7 @@ int scl_batch_destroy(scl_batch* b) {
         std::lock_guard<std::recursive_mutex> g(b->ctx->mu);
         cudaSetDevice(b->ctx->device);
         cudaDeviceSynchronize();
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        if (b->graph) cudaGraphDestroy(b->graph);
-        if (b->img.block) b->ctx->arena.release(b->img.block);
+        batch_release(b);
     }
     delete b;
     return SCL_OK;

@@ -200,6 +200,7 @@ struct Ctx {
                           Shape{512, 4, 0, PATH_LDG, 0}, Shape{256, 8, 0, PATH_LDG, 0}};
     std::map<const void*, int> occ_cache;
     int large_path = SCL_LARGE_AUTO;   // scl_set_large_path
+    int batch_split = 1;               // scl_set_batch_split
     // Scratch of single-partition launches, one per stream, so that launches
     // on different streams may overlap on the device.
     std::unordered_map<cudaStream_t, Scratch> single_by_stream;

@@ -168,6 +168,7 @@ _SIGS = {
     "scl_wrap_device": ([_P, _P, _P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_alloc_partition": ([_P, ctypes.c_int, _u64, ctypes.POINTER(_u64)], ctypes.c_int),
     "scl_set_large_path": ([_P, ctypes.c_int], ctypes.c_int),
+    "scl_set_batch_split": ([_P, ctypes.c_int], ctypes.c_int),
     "scl_free_partition": ([_P, _u64], ctypes.c_int),
     "scl_reload_partition": ([_P, _u64, _P, _P, _P], ctypes.c_int),
     "scl_partition_info": ([_P, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
@@ -320,6 +321,12 @@ SCL_LARGE_AUTO, SCL_LARGE_PACKED, SCL_LARGE_PARTITIONED, SCL_LARGE_DIRECT = 0, 1
 def scl_set_large_path(ctx: int, path: int) -> None:
     """Path of this context's later large-key reduces (SCL_LARGE_*)."""
     _check(lib.scl_set_large_path(ctx, path))
+
+
+def scl_set_batch_split(ctx: int, on: bool) -> None:
+    """Whether later batches mixing families launch one kernel per family,
+    concurrently (the default), or one mixed kernel."""
+    _check(lib.scl_set_batch_split(ctx, int(bool(on))))
 
 
 def scl_alloc_partition(ctx: int, dtype: int, n: int) -> int:

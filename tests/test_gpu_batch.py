@@ -4,7 +4,9 @@ Each task's result in a batch must match the oracle, and must equal the same
 task run alone: bitwise for integer sums, fp32/fp64 sums and min/max (fp32
 tasks see the same segment geometry and the same fixed-order fold in both),
 counts bitwise and sums within tolerance for keyed tasks.  Graph replays must
-give the same results launch after launch.
+give the same results launch after launch.  Batches that mix families run
+both ways: split into concurrent per-family launches (the default) and as one
+mixed-kernel launch; the two agree bitwise on the streaming tasks.
 """
 from __future__ import annotations
 
@@ -73,8 +75,10 @@ def check_batch(scl, specs, data, outs, res):
             assert int(r["u64_sum"]) == s.n and int(r["status"]) == 0
 
 
-def test_mixed_batch_matches_oracle_and_alone(env):
+@pytest.mark.parametrize("split", [True, False])
+def test_mixed_batch_matches_oracle_and_alone(env, split):
     c, scl, st, torch = env
+    scl.scl_set_batch_split(c.handle, split)
     rng = np.random.default_rng(200)
     sizes = [0, 1, 255, 256, 4097, 65_536, 1_000_003, 3_000_000, 17, 123_456, 8_388_608, 999]
     specs = [synth.TaskSpec(int(k), n, 1000 + i)
@@ -94,6 +98,7 @@ def test_mixed_batch_matches_oracle_and_alone(env):
         assert r.f64_sum == float(res[i]["f64_sum"]) or (np.isnan(r.f64_sum)), i
         assert np.float32(r.f32_min) == res[i]["f32_min"] and \
             np.float32(r.f32_max) == res[i]["f32_max"], i
+    scl.scl_set_batch_split(c.handle, True)
 
 
 @pytest.mark.parametrize("kind", [synth.KIND_MIX32, synth.KIND_POLY3, synth.KIND_KEYED])
@@ -106,12 +111,15 @@ def test_homogeneous_batches(env, kind):
     check_batch(scl, specs, data, outs, res)
 
 
-def test_graph_replays_are_identical(env):
+@pytest.mark.parametrize("split", [True, False])
+def test_graph_replays_are_identical(env, split):
     c, scl, st, torch = env
     specs = synth.batch_tasks(count=300, seed=9)
     parts, data, outs, tasks = make_batch(c, scl, st, torch, specs)
     arr = scl.make_tasks(tasks)
+    scl.scl_set_batch_split(c.handle, split)
     b = scl.scl_batch_create(c.handle, arr, len(tasks))
+    scl.scl_set_batch_split(c.handle, True)
     s2 = torch.cuda.Stream()
     scl.scl_batch_capture(b, s2.cuda_stream)
     first = None
@@ -125,8 +133,26 @@ def test_graph_replays_are_identical(env):
             streaming = np.array([s.kind != synth.KIND_KEYED for s in specs])
             assert np.array_equal(res[streaming], first[streaming])
             assert np.array_equal(res["u64_sum"], first["u64_sum"])
-    assert scl.scl_batch_kernel_launches(b) in (1, 2)
+    # split: a kernel per family (3) and the keyed fold; mixed: one and the fold
+    assert scl.scl_batch_kernel_launches(b) in ((3, 4) if split else (1, 2))
     scl.scl_batch_destroy(b)
+
+
+def test_split_and_mixed_launches_agree(env):
+    c, scl, st, torch = env
+    specs = synth.batch_tasks(count=500, seed=21)
+    parts, data, outs, tasks = make_batch(c, scl, st, torch, specs)
+    arr = scl.make_tasks(tasks)
+    got = {}
+    for split in (True, False):
+        scl.scl_set_batch_split(c.handle, split)
+        got[split] = scl.scl_batch_run(c.handle, arr, len(tasks), stream=st)
+        check_batch(scl, specs, data, outs, got[split])
+    scl.scl_set_batch_split(c.handle, True)
+    streaming = np.array([s.kind != synth.KIND_KEYED for s in specs])
+    assert np.array_equal(got[True][streaming], got[False][streaming])
+    assert np.array_equal(got[True]["u64_sum"], got[False]["u64_sum"])
+    assert scl.lib.scl_set_batch_split(c.handle, 2) == scl.SCL_E_INVALID
 
 
 def test_single_task_and_empty_batches(env):
