@@ -435,7 +435,8 @@ typedef struct {
     int32_t block;             /* data threads per CTA: 256 or 512               */
     int32_t items_per_thread;  /* 128-bit vectors per thread per chunk: 2, 4, 8  */
     int32_t ctas_per_sm;       /* resident CTAs per SM; 0 = as many as fit       */
-    int32_t path;              /* 0 = vector loads, 1 = TMA bulk-copy pipeline   */
+    int32_t path;              /* 0 = vector loads, 1 = TMA bulk-copy pipeline,
+                                  2 = keyed 512x2 capped at 48 registers        */
     int32_t stages;            /* TMA ring depth; 0 = the shape's default        */
     int32_t reserved;
 } scl_shape;
@@ -485,9 +486,10 @@ int scl_autotune(scl_ctx* ctx, const scl_autotune_config* cfg, void* stream,
  * (pairs plus a fixed cost per piece) over the CTAs that take keyed pieces.
  * A batch whose tasks mix families (uint32, fp32, keyed) launches, with
  * splitting on (the default, scl_set_batch_split), one persistent kernel per
- * family, concurrently: the keyed-only kernel first on `stream`, the others
- * on two side streams the batch owns, forked from `stream` and joined back
- * into it.  With splitting off it is one launch of the mixed kernel, a
+ * family, concurrently: the keyed-only kernel first on `stream` (512-thread
+ * CTAs capped at 48 registers, two per SM, so that two streaming CTAs stay
+ * resident beside them on every SM), the others on two side streams the
+ * batch owns, forked from `stream` and joined back into it.  With splitting off it is one launch of the mixed kernel, a
  * cost-weighted share of whose CTAs take the keyed pieces while the rest
  * stream.  The plan, task table and scratch are placed in the arena; nothing
  * runs yet.

@@ -1048,7 +1048,10 @@ int scl_batch_create(scl_ctx* ctx, const scl_task* tasks, uint32_t ntasks, scl_b
             b->order.push_back(i);
             sub.push_back(tasks[i]);
         }
-        st = plan_tasks(ctx, sub.data(), G.count, &G.plan);
+        // keyed tasks beside streaming groups: the register-capped keyed kernel
+        const Shape lean{kLeanKeyedBlock, kLeanKeyedIpt, 2, PATH_LEAN, 0};
+        const bool beside = ng > 1 && fam[g].size() && is_keyed(all.tasks[fam[g][0]].kind);
+        st = plan_tasks(ctx, sub.data(), G.count, &G.plan, beside ? &lean : nullptr);
         if (st != SCL_OK) return bail(st);
         ExternalScratch ext;
         ext.results = b->results + G.first;

@@ -338,7 +338,10 @@ struct KernelEntry {
     int stages;                        // TMA ring stages (0 for LDG)
 };
 
-enum Path : int { PATH_LDG = 0, PATH_TMA = 1 };
+// PATH_LEAN: the keyed-only kernel capped at kKeyedLeanRegs registers.
+enum Path : int { PATH_LDG = 0, PATH_TMA = 1, PATH_LEAN = 2 };
+constexpr int kKeyedLeanRegs = 48;
+constexpr int kLeanKeyedBlock = 512, kLeanKeyedIpt = 2;   // its one compiled shape
 
 // Threads launched per CTA: TMA kernels add one producer warp.
 inline int launch_threads(const KernelEntry& e) { return e.block + (e.path == PATH_TMA ? 32 : 0); }

@@ -800,8 +800,7 @@ constexpr int persistent_min_blocks() {
 }
 
 template <int BLOCK, int IPT, int MASK>
-__global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT>()))
-    k_persistent(const __grid_constant__ KernelArgs a) {
+__device__ __forceinline__ void persistent_body(const KernelArgs& a) {
     __shared__ RedSmem sm;
     extern __shared__ uint4 dyn_smem[];
 
@@ -889,6 +888,22 @@ __global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT
             if (a.err_out) *a.err_out = atomicOr(&a.hdr[H_ERROR], 0u);
         }
     }
+}
+
+template <int BLOCK, int IPT, int MASK>
+__global__ void __launch_bounds__(BLOCK, (persistent_min_blocks<MASK, BLOCK, IPT>()))
+    k_persistent(const __grid_constant__ KernelArgs a) {
+    persistent_body<BLOCK, IPT, MASK>(a);
+}
+
+// The keyed-only kernel held to kKeyedLeanRegs registers per thread, for a
+// batch whose streaming tasks run concurrently in kernels of their own: two
+// 512-thread CTAs of it take 48 Ki of an SM's 64 Ki registers, so two
+// 256-thread streaming CTAs (32 registers) stay resident beside them and
+// stream from DRAM while the keyed CTAs are bound by shared-memory atomics.
+template <int BLOCK, int IPT>
+__global__ void __maxnreg__(kKeyedLeanRegs) k_keyed_lean(const __grid_constant__ KernelArgs a) {
+    persistent_body<BLOCK, IPT, M_KEYED>(a);
 }
 
 // --------------------------------------------------------- keyed fold pass
@@ -1316,6 +1331,9 @@ __global__ void __launch_bounds__(FB) k_keyed_large_finish(const __grid_constant
      : scl::mask_has_keyed(M)     ? scl::kKeyedSmemBytes         \
                                   : 0)
 #define SCL_SHAPE(M, B, I) {M, B, I, (const void*)&scl::dev::k_persistent<B, I, M>, SCL_DYN(M), 0, 0}
+#define SCL_LEAN_SHAPE(B, I)                                                         \
+    {scl::M_KEYED, B, I, (const void*)&scl::dev::k_keyed_lean<B, I>, scl::kKeyedFastSmemBytes, \
+     scl::PATH_LEAN, 0}
 #define SCL_DEFINE_TABLE(NAME, M)                                                   \
     namespace scl {                                                                 \
     const KernelEntry* kernel_table_##NAME(int* count) {                            \

@@ -20,6 +20,7 @@ namespace scl {
 const KernelEntry* kernel_table_u32(int* count);
 const KernelEntry* kernel_table_f32(int* count);
 const KernelEntry* kernel_table_keyed(int* count);
+const KernelEntry* kernel_table_keyed_lean(int* count);
 const KernelEntry* kernel_table_all(int* count);
 const KernelEntry* kernel_table_tma_u32(int* count);
 const KernelEntry* kernel_table_tma_f32(int* count);
@@ -126,6 +127,9 @@ const KernelEntry* find_entry(int mask, int block, int ipt, int path, int stages
         if (mask == M_U32) t = kernel_table_tma_u32(&n);
         else if (mask == M_F32) t = kernel_table_tma_f32(&n);
         else return nullptr;
+    } else if (path == PATH_LEAN) {
+        if (mask != M_KEYED) return nullptr;
+        t = kernel_table_keyed_lean(&n);
     } else {
         t = table(mask, &n);
     }
@@ -382,7 +386,7 @@ static uint64_t keyed_piece_overhead(int mask, const Shape& s) {
     return (uint64_t)s.block * (mask == M_KEYED ? kKeyedPieceOverheadFast : kKeyedPieceOverheadMixed);
 }
 
-int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
+int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P, const Shape* shape) {
     P->tasks.assign(nt, DevTask{});
     bool has_u32 = false, has_f32 = false, has_keyed = false;
     std::vector<uint32_t> kind(nt);
@@ -410,7 +414,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P) {
     }
     const int ntypes = (int)has_u32 + (int)has_f32 + (int)has_keyed;
     P->mask = ntypes > 1 ? M_ALL : has_keyed ? M_KEYED : has_f32 ? M_F32 : M_U32;
-    P->shape = c->shape_for(P->mask);
+    P->shape = shape ? *shape : c->shape_for(P->mask);
     if (!find_entry(P->mask, P->shape))
         return fail(SCL_E_STATE, "no kernel for shape %d x %d", P->shape.block, P->shape.ipt);
     const uint32_t gmax = c->grid_max(P->mask, P->shape);

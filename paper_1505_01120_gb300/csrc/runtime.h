@@ -133,7 +133,9 @@ struct Plan {
 struct Ctx;
 // Build the launch plan of `tasks` (validated).  Result pointers of the
 // DevTasks are left null; the caller points them at its result array.
-int plan_tasks(Ctx* c, const scl_task* tasks, uint32_t n, Plan* out);
+// `shape`, if set, replaces the context's shape for the plan's kernel family.
+int plan_tasks(Ctx* c, const scl_task* tasks, uint32_t n, Plan* out,
+               const Shape* shape = nullptr);
 
 // Device image of a plan plus its own scratch, in one arena block.
 struct PlanImage {
