@@ -57,6 +57,13 @@ PARTS, PART_N = 64, 4_194_304
 STEP_BYTES = PARTS * PART_N * 4
 WORKLOAD = "poly3_sum_min_max_64x4194304_f32"
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_persistent_f32_poly3_64x4194304.md")
+# The keyed reduce's ceiling other than HBM: pairs per second of a loop that
+# loads 128-bit key and value vectors and makes two shared-memory integer adds
+# per pair (a count and a fixed-point sum) into a 4096-entry table, 268 M
+# uniform pairs, measured on GB300 (the keyed kernel's loop without its fp32
+# path).  A loop with the loads and no atomics ran at 766 G pairs/s.
+KEYED_ATOMIC_CEILING = 753e9
+
 KERNEL_SOURCES = ["paper_1505_01120_gb300/csrc/kernels.cuh",
                   "paper_1505_01120_gb300/csrc/internal.h"]
 
@@ -367,6 +374,11 @@ def extra_configs(torch, scl, ctx, stream, pk, serve_secs: float) -> dict:
     out["keyed_count_sum_16x16777216"] = {
         "gbs": 16 * m * 8 / ms / 1e6, "frac_of_hbm": 16 * m * 8 / ms / 1e6 / pk, "ms": ms,
         "pairs_per_s": 16 * m / ms * 1e3,
+        "frac_of_atomic_ceiling": 16 * m / ms * 1e3 / KEYED_ATOMIC_CEILING,
+        "atomic_ceiling": {"pairs_per_s": KEYED_ATOMIC_CEILING, "gbs": KEYED_ATOMIC_CEILING * 8e-9,
+                           "what": "shared-memory atomic pipe: a u32 count add and a u32 "
+                                   "fixed-point sum add per pair, 268 M uniform pairs over "
+                                   "4096 keys, loads included (probe on GB300)"},
         "partition0_counts_exact": bool(np.array_equal(o0[:4096].view(np.uint32), ocnt)),
         "partition0_max_rel_err": float(np.max(np.abs(s64 - osum) / np.abs(osum)))}
     scl.scl_batch_destroy(b)
