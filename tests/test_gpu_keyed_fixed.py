@@ -6,7 +6,8 @@ the largest value of the piece's first chunk.  Other values take fp32 adds.
 A window in which one key takes 512 pairs or more makes the piece run again
 on the fp32 table.  These cases cover values on both sides of the window,
 zeros of both signs, negative values, NaN and inf, a first chunk much smaller
-than the rest, a key that overflows a window, and hashed keys.  Counts must
+than the rest, a key that overflows a window, Zipf keys (most pairs on the
+head ids below 32), and hashed keys.  Counts must
 be exact and sums within 1e-5 of the fp64 oracle.  Non-finite sums must match
 the oracle's (NaN where it has NaN, the same infinity).
 """
@@ -125,6 +126,26 @@ def test_hashed_keys(env):
     assert np.array_equal(cnt, ocnt)
     nz = ocnt > 0
     assert np.all(np.abs(s64[nz] - osum[nz]) <= REL * np.abs(osum[nz]))
+
+
+@pytest.mark.parametrize("n", [1_000_003, 16_777_216])
+def test_zipf_head_ids(env, n):
+    # Zipf(1.2) keys put ~2/3 of the pairs on ids below 32, which take the
+    # fp32 head copies while the other ids' in-window values take the int32
+    # table.  Some head values are moved below and above the window, some
+    # negated.
+    from paper_1505_01120_gb300 import synth
+    rng = np.random.default_rng(508)
+    keys = synth.zipf_keys_i32(n, rng, 4096)
+    vals = rng.random(n, dtype=np.float32)
+    hot = np.nonzero(keys < 32)[0]
+    sel = rng.choice(hot, size=len(hot) // 50, replace=False)
+    q = len(sel) // 3
+    vals[sel[:q]] *= np.float32(1e-4)
+    vals[sel[q:2 * q]] = -vals[sel[q:2 * q]]
+    vals[sel[2 * q:]] += np.float32(3.0)
+    cnt, sums, s64 = _run(env, keys, vals, 4096)
+    assert check_keyed(cnt, sums, s64, keys, vals, 4096) == 0
 
 
 def test_repeat_calls_agree(env):
