@@ -76,6 +76,10 @@ constexpr uint64_t kKeyedPieceOverheadMixed = 16;   // per thread of a mixed-ker
 constexpr uint32_t kMaxSegChunks = 4;               // a streaming segment is 1..4 chunks
 constexpr uint32_t kTargetSegsPerTask = 256;
 constexpr uint32_t kFoldBlock = 256;                // keyed fold kernel block size
+// A keyed task of at most this many pieces is folded by the CTA that writes
+// its last piece table; one of more pieces by k_keyed_fold, whose CTAs split
+// the ids (a task of many pieces ends with all of them, at the kernel's end).
+constexpr uint32_t kFoldInKernelMaxPieces = 8;
 
 // Work kinds: (map kernel, reduce) combinations of the catalogue.
 enum Kind : uint32_t {

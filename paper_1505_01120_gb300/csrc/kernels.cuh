@@ -717,10 +717,86 @@ __device__ __forceinline__ int keyed_accumulate(const DevTask& t, uint64_t b, ui
     return any_bad;
 }
 
+// The fold of a keyed task cut into t.nseg pieces, by the CTA that wrote its
+// last piece table: per id, the counts (exact, uint32) and the fp32 sums (a
+// float-float pair) over the tables in piece order; then the outputs, and the
+// result with the totals.  Four consecutive ids per thread are read as 16-byte
+// vectors, four pieces' loads in flight at a time.  Call between barriers.
+template <int BLOCK>
+__device__ __forceinline__ void keyed_fold_task(const KernelArgs& a, const DevTask& t,
+                                                uint32_t task, RedSmem& sm) {
+    const uint32_t nk = t.num_keys, np = t.nseg;
+    const uint32_t* base = a.kpart + (size_t)t.slot0 * kKeyedTableWords;
+    unsigned long long ctot = 0;
+    ff stot{0.f, 0.f};
+    auto put = [&](uint32_t k, uint32_t c, ff s) {
+        const double sd = ff_to_double(s);
+        t.counts_out[k] = c;
+        t.sums_out[k] = (float)sd;
+        if (t.sums64_out) t.sums64_out[k] = sd;
+        ctot += c;
+        stot = ff_add(stot, s);
+    };
+    for (uint32_t q = threadIdx.x; q < nk / 4; q += BLOCK) {
+        uint4 c{0u, 0u, 0u, 0u};
+        ff s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        uint32_t p = 0;
+        for (; p + 4 <= np; p += 4) {
+            uint4 cc[4], sv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint32_t* tb = base + (size_t)(p + r) * kKeyedTableWords;
+                cc[r] = __ldcg(reinterpret_cast<const uint4*>(tb) + q);
+                sv[r] = __ldcg(reinterpret_cast<const uint4*>(tb + kMaxKeys) + q);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                c.x += cc[r].x; c.y += cc[r].y; c.z += cc[r].z; c.w += cc[r].w;
+                s[0] = ff_add_f(s[0], __uint_as_float(sv[r].x));
+                s[1] = ff_add_f(s[1], __uint_as_float(sv[r].y));
+                s[2] = ff_add_f(s[2], __uint_as_float(sv[r].z));
+                s[3] = ff_add_f(s[3], __uint_as_float(sv[r].w));
+            }
+        }
+        for (; p < np; ++p) {
+            const uint32_t* tb = base + (size_t)p * kKeyedTableWords;
+            const uint4 cc = __ldcg(reinterpret_cast<const uint4*>(tb) + q);
+            const uint4 sv = __ldcg(reinterpret_cast<const uint4*>(tb + kMaxKeys) + q);
+            c.x += cc.x; c.y += cc.y; c.z += cc.z; c.w += cc.w;
+            s[0] = ff_add_f(s[0], __uint_as_float(sv.x));
+            s[1] = ff_add_f(s[1], __uint_as_float(sv.y));
+            s[2] = ff_add_f(s[2], __uint_as_float(sv.z));
+            s[3] = ff_add_f(s[3], __uint_as_float(sv.w));
+        }
+        put(4 * q, c.x, s[0]);
+        put(4 * q + 1, c.y, s[1]);
+        put(4 * q + 2, c.z, s[2]);
+        put(4 * q + 3, c.w, s[3]);
+    }
+    for (uint32_t k = nk / 4 * 4 + threadIdx.x; k < nk; k += BLOCK) {
+        uint32_t c = 0;
+        ff s{0.f, 0.f};
+        for (uint32_t p = 0; p < np; ++p) {
+            const uint32_t* tb = base + (size_t)p * kKeyedTableWords;
+            c += __ldcg(tb + k);
+            s = ff_add_f(s, __uint_as_float(__ldcg(tb + kMaxKeys + k)));
+        }
+        put(k, c, s);
+    }
+    block_reduce_ff_u64<BLOCK>(stot, ctot, sm);
+    if (threadIdx.x == 0) {
+        const uint32_t fl = atomicExch(&a.task_flags[task], 0u);
+        write_result(t.result, ctot, ff_to_double(stot), CUDART_INF_F, -CUDART_INF_F,
+                     fl ? SCL_E_KEY_RANGE : SCL_OK, t.n, t.kind);
+        a.tickets[task] = 0u;
+    }
+}
+
 // One keyed piece: pairs [b, e) of task `task`, accumulated into the CTA's
 // shared-memory table (count, fp32 sum) and written to the outputs (single
-// piece) or to partial slot slot0 + slot.  Returns true in thread 0 if it
-// wrote the task's result (single piece).
+// piece) or to partial slot slot0 + slot; the last writer of a task of at
+// most kFoldInKernelMaxPieces pieces folds it.  Returns true in thread 0 if
+// it wrote the task's result.
 template <int BLOCK, int IPT, bool HASHED, bool FAST>
 __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& t, uint32_t task,
                                             uint32_t slot, uint64_t b, uint64_t e,
@@ -778,6 +854,19 @@ __device__ __forceinline__ bool keyed_piece(const KernelArgs& a, const DevTask& 
             __stcg(dst + kMaxKeys + k, __float_as_uint(sum[k]));
         }
         if (any_bad && threadIdx.x == 0) atomicOr(&a.task_flags[task], 1u);
+        // a task of few pieces: one ticket per written piece table; the CTA
+        // that writes the last one folds the task (more pieces: k_keyed_fold)
+        if (t.nseg <= kFoldInKernelMaxPieces) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) sm.flag = atomicAdd(&a.tickets[task], 1u) == t.nseg - 1;
+            __syncthreads();
+        }
+        if (t.nseg <= kFoldInKernelMaxPieces && sm.flag) {
+            __threadfence();
+            keyed_fold_task<BLOCK>(a, t, task, sm);
+            wrote = threadIdx.x == 0;
+        }
     }
     __syncthreads();   // the table is re-zeroed by the next piece
     return wrote;

@@ -365,7 +365,7 @@ int run_single(Ctx* c, const Partition& p, uint32_t kind, const float* coef, uin
     a.hdr = sc.hdr;
     a.err_out = err_out;
     SCL_TRY(launch_entry(e, grid, a, st));
-    if (is_keyed(kind) && t.nseg > 1) {
+    if (is_keyed(kind) && t.nseg > kFoldInKernelMaxPieces) {   // else its last piece folds it
         const uint32_t nkb = (nk + kFoldBlock - 1) / kFoldBlock;
         void* params[] = {&a};
         SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(nkb, 1), dim3(kFoldBlock), params, 0, st));
@@ -487,7 +487,7 @@ int plan_tasks(Ctx* c, const scl_task* in, uint32_t nt, Plan* P, const Shape* sh
             t.slot0 = P->kslots;
             if (t.nseg > 1) {
                 P->kslots += t.nseg;
-                P->fold_tasks.push_back(i);
+                if (t.nseg > kFoldInKernelMaxPieces) P->fold_tasks.push_back(i);
             }
             k = e;
         }
@@ -585,7 +585,7 @@ int launch_plan(Ctx* c, const Plan& p, const KernelArgs& args, cudaStream_t st) 
     const KernelEntry* e = find_entry(p.mask, p.shape);
     if (!e) return fail(SCL_E_STATE, "no kernel for the plan's shape");
     SCL_TRY(launch_entry(e, p.grid, args, st));
-    if (!p.fold_tasks.empty()) {
+    if (!p.fold_tasks.empty()) {   // keyed tasks of many pieces; the others fold in the kernel
         void* params[] = {const_cast<KernelArgs*>(&args)};
         SCL_CUDA(cudaLaunchKernel(fold_kernel_fn(), dim3(p.fold_gridx, (uint32_t)p.fold_tasks.size()),
                                   dim3(kFoldBlock), params, 0, st));
