@@ -5,17 +5,23 @@
 //                                   mapped by the catalogue kernel (the run()
 //                                   body of Sec. 3.1.1.2) and folded, in one
 //                                   HBM pass, by a persistent grid.
+//   k_keyed_lean<BLOCK, IPT>        the keyed-only persistent kernel capped at 48
+//                                   registers, for keyed tasks that share the SMs
+//                                   with a concurrent streaming launch.
 //   k_keyed_fold                    second pass of the keyed reduce (Sec. 3.2.3):
-//                                   folds the per-piece tables of keyed tasks.
+//                                   folds the per-piece tables of keyed tasks cut
+//                                   into more than 8 pieces (fewer: the CTA that
+//                                   writes the last piece folds them).
 //   k_map<BLOCK, IPT, KIND, ALIGNED> MapCL with a materialised output array
 //                                   (Sec. 3.1.3 item 1; Fig. 3's c[gid] = f(a[gid])).
 //
 // Data path: 128-bit vector loads (ld.global.nc, no L1 allocation, 256-byte L2
 // prefetch) of IPT independent vectors per thread before any use, so a CTA
 // has BLOCK*IPT*16 bytes in flight; streaming sums are fp32 per thread per
-// chunk, fp64 across chunks, a fixed-order warp-butterfly and block tree, one
-// partial per segment and one atomic ticket per task; the last CTA of a task
-// folds the segment partials in slot order (deterministic).
+// chunk, float-float pairs across chunks (the fp32 pipe, not GB300's slow
+// fp64 pipe), a fixed-order warp-butterfly and block tree, one partial per
+// segment and one atomic ticket per task; the last CTA of a task folds the
+// segment partials in slot order (deterministic).
 #pragma once
 
 #include <cuda_runtime.h>
