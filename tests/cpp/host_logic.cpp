@@ -96,8 +96,12 @@ static void check_keyed_plan() {
                                 [](const auto& a, const auto& b) { return a.first == b.first; }),
                     keyed.end());
         const uint32_t Gk = 1 + (uint32_t)(rng() % 1216);
+        // the per-piece cost the batch planner charges: the default, and 16 or
+        // 32 pair-equivalents per thread of a 256- or 512-thread CTA
+        const uint64_t overheads[] = {kKeyedTaskOverhead, 4096, 8192, 16384};
+        const uint64_t overhead = overheads[rng() % 4];
         std::vector<KeyedPlanPiece> out;
-        plan_keyed_pieces(keyed, Gk, &out);
+        plan_keyed_pieces(keyed, Gk, &out, overhead);
         size_t k = 0;
         uint32_t last_cta = 0;
         for (const auto& t : keyed) {
