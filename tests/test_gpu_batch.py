@@ -172,3 +172,56 @@ def test_one_big_and_many_tiny(env):
     parts, data, outs, tasks = make_batch(c, scl, st, torch, specs)
     res = scl.scl_batch_run(c.handle, scl.make_tasks(tasks), len(tasks), stream=st)
     check_batch(scl, specs, data, outs, res)
+
+
+@pytest.mark.parametrize("kinds", [(synth.KIND_MIX32, synth.KIND_KEYED),
+                                   (synth.KIND_POLY3, synth.KIND_KEYED),
+                                   (synth.KIND_MIX32, synth.KIND_POLY3)])
+def test_two_family_batches(env, kinds):
+    # split into two concurrent launch groups (the keyed one, if any, on the
+    # 48-register kernel)
+    c, scl, st, torch = env
+    sizes = [3_000_000, 200_000, 20_000, 4097, 0, 1_000_003]
+    specs = [synth.TaskSpec(kinds[i % 2], n, 700 + i) for i, n in enumerate(sizes)]
+    parts, data, outs, tasks = make_batch(c, scl, st, torch, specs)
+    arr = scl.make_tasks(tasks)
+    b = scl.scl_batch_create(c.handle, arr, len(tasks))
+    assert scl.scl_batch_kernel_launches(b) in (2, 3)
+    s2 = torch.cuda.Stream()   # capture needs a stream other than the legacy default
+    scl.scl_batch_capture(b, s2.cuda_stream)
+    scl.scl_batch_launch(b, s2.cuda_stream)
+    res = scl.scl_batch_results(b, len(tasks), stream=s2.cuda_stream)
+    scl.scl_batch_destroy(b)
+    check_batch(scl, specs, data, outs, res)
+
+
+@pytest.mark.parametrize("n", [20_000, 200_000, 3_000_000])
+def test_split_batch_key_out_of_range(env, n):
+    # one keyed piece (20 K pairs), a few pieces folded by the last writer
+    # (200 K), many pieces folded by k_keyed_fold (3 M): a bad key is reported,
+    # and the next launch of a clean batch is not affected
+    c, scl, st, torch = env
+    rng = np.random.default_rng(800 + n % 97)
+    keys = rng.integers(0, 4096, size=n, dtype=np.int32)
+    keys[[1, n - 1]] = [-5, 4096]
+    vals = rng.random(n, dtype=np.float32)
+    pk = scl.scl_load_partition_kv(c.handle, keys, vals, stream=st)
+    o = (torch.zeros(4096, dtype=torch.int32, device="cuda"),
+         torch.zeros(4096, dtype=torch.float32, device="cuda"))
+    specs = [synth.TaskSpec(synth.KIND_MIX32, 100_000, 901), synth.TaskSpec(synth.KIND_POLY3, 70_000, 902)]
+    parts, data, outs, tasks = make_batch(c, scl, st, torch, specs)
+    bad = dict(part=pk, kernel=scl.SCL_K_IDENT, reduce=scl.SCL_R_KEYED_COUNT_SUM, num_keys=4096,
+               counts_out=o[0], sums_out=o[1])
+    with pytest.raises(scl.SclError) as e:
+        scl.scl_batch_run(c.handle, scl.make_tasks(tasks + [bad]), 3, stream=st)
+    assert e.value.status == scl.SCL_E_KEY_RANGE
+    res = scl.scl_batch_run(c.handle, scl.make_tasks(tasks + [bad]), 3, stream=st,
+                            allow_key_range=True)
+    assert int(res[2]["status"]) == scl.SCL_E_KEY_RANGE and int(res[2]["u64_sum"]) == n - 2
+    assert int(res[0]["status"]) == 0 and int(res[1]["status"]) == 0
+    check_batch(scl, specs, data, outs, res[:2])
+    cnt = o[0].cpu().numpy().view(np.uint32)
+    ocnt, _, _ = oracle.keyed_count_sum(keys, vals, 4096)
+    assert np.array_equal(cnt, ocnt)   # the bad keys are dropped, the rest counted
+    res = scl.scl_batch_run(c.handle, scl.make_tasks(tasks), 2, stream=st)
+    check_batch(scl, specs, data, outs, res)
