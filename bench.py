@@ -64,6 +64,12 @@ PROFILE_MD = os.path.join(ROOT, "profiles", "k_persistent_f32_poly3_64x4194304.m
 # path).  A loop with the loads and no atomics ran at 766 G pairs/s.
 KEYED_ATOMIC_CEILING = 753e9
 
+# The packed large-key path's ceiling other than HBM: pairs per second of a
+# loop that loads 128-bit key and value vectors and makes one 64-bit L2 atomic
+# add per pair, 64 Mi pairs over 2^20 uniform keys, measured on GB300 (177-193
+# G/s; the upper figure).
+LARGE_L2_ATOMIC_CEILING = 193e9
+
 KERNEL_SOURCES = ["paper_1505_01120_gb300/csrc/kernels.cuh",
                   "paper_1505_01120_gb300/csrc/internal.h"]
 
@@ -843,7 +849,9 @@ def keyed_large_config(torch, scl, ctx, stream, pk: float) -> dict:
         scl.scl_free_partition(ctx.handle, p)
         out[name] = {"path": "packed direct (automatic choice)",
                      "gbs": 8 * n / ms / 1e6, "frac_of_hbm": 8 * n / ms / 1e6 / pk, "ms": ms,
-                     "pairs_per_s": n / ms * 1e3, "counts_exact": exact,
+                     "pairs_per_s": n / ms * 1e3,
+                     "frac_of_l2_atomic_ceiling": n / ms * 1e3 / LARGE_L2_ATOMIC_CEILING,
+                     "counts_exact": exact,
                      "partitioned_ms": ms_part, "partitioned_counts_exact": exact_part}
     return out
 
