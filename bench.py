@@ -274,12 +274,17 @@ class Timer:
         return float(np.mean([a.elapsed_time(b) for a, b in self.ev]))
 
 
-def time_device(torch, stream, fn, reps: int, warm: int = 3, flush=None) -> float:
-    """Median ms of fn() by CUDA events on `stream`, optional L2 flush before each."""
+def time_device(torch, stream, fn, reps: int, warm: int = 3, flush=None,
+                back_to_back: bool = True) -> float:
+    """Median ms of fn() by CUDA events on `stream`, optional L2 flush before each.
+    back_to_back: the reps are enqueued one after another and read after one
+    synchronisation, so the device does not sit idle at the start of a rep
+    waiting for the host to enqueue it (fn must not synchronise); otherwise
+    each rep is waited for before the next is enqueued."""
     for _ in range(warm):
         fn()
     torch.cuda.synchronize()
-    ts = []
+    evs = []
     with torch.cuda.stream(stream):
         for _ in range(reps):
             if flush is not None:
@@ -289,9 +294,11 @@ def time_device(torch, stream, fn, reps: int, warm: int = 3, flush=None) -> floa
             a.record(stream)
             fn()
             b.record(stream)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-    return float(np.median(ts))
+            if not back_to_back:
+                b.synchronize()
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in evs]))
 
 
 def extra_configs(torch, scl, ctx, stream, pk, serve_secs: float) -> dict:
@@ -322,7 +329,7 @@ def extra_configs(torch, scl, ctx, stream, pk, serve_secs: float) -> dict:
     call = lambda: scl.scl_map_reduce_async(  # noqa: E731
         ctx.handle, p, scl.SCL_K_MIX32, scl.SCL_R_SUM, dres.data_ptr(), stream=st)
     # events around one host call: the device idles while the host enqueues
-    enq_us = time_device(torch, stream, call, 50) * 1e3
+    enq_us = time_device(torch, stream, call, 50, back_to_back=False) * 1e3
     # device time per call: 20 calls captured back to back in a CUDA graph
     call()
     torch.cuda.synchronize()
